@@ -1,0 +1,61 @@
+/*
+ * rewl_oracle.h -- interface of the plain CPU oracle for replica-exchange
+ * Wang-Landau sampling.  TEST INFRASTRUCTURE ONLY: used by tests/,
+ * __graft_entry__.smoke() and bench.py's CPU baseline; never by the library.
+ */
+#ifndef REWL_ORACLE_H
+#define REWL_ORACLE_H
+#include <stdint.h>
+
+enum { ORC_ISING = 0, ORC_POTTS = 1, ORC_EA = 2 };
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_EENTRY = 5 };
+
+typedef struct {
+  int sweeps_per_exchange;    /* sweeps between exchange rounds (100) */
+  int sweeps_per_flat_check;  /* sweeps between flatness checks (1000), a multiple of the above */
+  double lnf0;                /* initial ln f (1.0) */
+  int entry_max_sweeps;       /* budget of each greedy entry walk (1000 sweeps) */
+  int discovery_sweeps;       /* +-J only: zero-temperature descent that fixes the energy range (200) */
+} orc_params;
+
+typedef struct orc_rewl {
+  int model, q, L, N;
+  int8_t *Jr, *Jd;            /* couplings of the bond to the right / below each site */
+  int e_min, e_max, e_step, n_bins;
+  int h, m, w;
+  double overlap, flatness, lnf_final;
+  uint64_t seed;
+  orc_params params;
+  int* win_start;             /* first global bin of each window */
+  double* lnf;
+  int *iter, *done;
+  uint8_t* spins;             /* [h*m][N] */
+  int* E;                     /* [h*m] */
+  double* lng;                /* [h*m][w] */
+  uint32_t* H;                /* [h*m][w] */
+  uint8_t* seed_config;       /* restart configuration for the entry walk */
+  uint64_t* entry_t;          /* per-walker counter of the entry stream */
+  uint64_t sweep_clock;
+  uint32_t xround;
+  uint64_t *wl_accept, *near_ties, *x_tried, *x_accepted;
+} orc_rewl;
+
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_default_params(orc_params* p);
+int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings, int h, double overlap, int m,
+               double flatness, double lnf_final, uint64_t seed, const orc_params* params);
+void orc_destroy(orc_rewl* R);
+int orc_run_blocks(orc_rewl* R, int64_t n_blocks, int* all_done);
+int orc_energy(const orc_rewl* R, const uint8_t* s);
+int orc_walker_is_flat(const orc_rewl* R, int W);
+void orc_info(const orc_rewl* R, int64_t* info);
+void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* iter, int32_t* done);
+void orc_get_walkers(const orc_rewl* R, uint8_t* spins, int32_t* E, double* lng, uint32_t* H);
+void orc_get_couplings(const orc_rewl* R, int8_t* J);
+void orc_get_counters(const orc_rewl* R, uint64_t* wl_accept, uint64_t* near_ties, uint64_t* x_tried,
+                      uint64_t* x_accepted);
+void orc_set_walker_lng(orc_rewl* R, int W, const double* lng);
+void orc_set_window_lnf(orc_rewl* R, int a, double lnf);
+void orc_set_walker_H(orc_rewl* R, int W, const uint32_t* H);
+
+#endif
