@@ -1,0 +1,353 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 REWL library: spin-flip attempts per second of the
+whole REWL pipeline (WL sweeps, exchange rounds, flatness checks and merges)
+on the Ising 32 x 32 workload with 16 windows x 4 walkers, ln f -> 1e-8.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+One step = one flatness period of the solve: 1000 sweeps of every active
+walker (10 blocks of 100 sweeps, each followed by an exchange round) and one
+flatness check / merge.  Inputs are resident on the device when the timed
+region starts; L2 is flushed (256 MiB written) between timed steps, outside
+the per-step CUDA events.  Under torchrun every rank runs an independent
+replica with its own seed (the method shards by independent solves; there is
+no data-path collective), value = all attempts / max time over ranks.
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ising-L32-h16-m4": dict(model="ising", L=32, q=2, h=16, m=4, lnf_final=1e-8,
+                             desc="2D Ising L=32 periodic J=1; 16 windows at 75% overlap x 4 walkers (64 walkers); "
+                                  "flatness 0.8 checked every 1000 sweeps; ln f 1 -> 1e-8; swaps every 100 sweeps"),
+    "ising-L8-h4-m2": dict(model="ising", L=8, q=2, h=4, m=2, lnf_final=1e-6,
+                           desc="2D Ising L=8; 4 windows at 75% overlap x 2 walkers; ln f 1 -> 1e-6"),
+    "potts-q10-L32-h32-m16": dict(model="potts", L=32, q=10, h=32, m=16, lnf_final=1e-8,
+                                  desc="2D q=10 Potts L=32; 32 windows at 75% overlap x 16 walkers (512 walkers); "
+                                       "ln f 1 -> 1e-8"),
+    "ising-L128-h128-m32": dict(model="ising", L=128, q=2, h=128, m=32, lnf_final=1e-6,
+                                desc="2D Ising L=128; 128 windows at 75% overlap x 32 walkers (4096 walkers); "
+                                     "ln f 1 -> 1e-6"),
+}
+DEFAULT_WORKLOAD = "ising-L32-h16-m4"
+OVERLAP, FLATNESS, SPE, SPF = 0.75, 0.8, 100, 1000
+METRIC = "spin-flip attempts/s (REWL: WL sweeps + exchange + flatness/merge)"
+# Minimal integer instructions of one WL trial on the sweep kernel's path:
+# Philox4x32-10 = 10 rounds x (2 IMAD.WIDE + 2 LOP3) = 40 with the round keys
+# held in registers; site, row and column 4; neighbour loads and the dE count
+# 12; bin, window test and the fixed-point acceptance test 6; shadow, H and
+# configuration updates 4.  Total 66 (the accounting is stated in the design doc).
+OPS_PER_ATTEMPT = 66
+LANES_PER_SM_PER_CLK = 128   # 4 schedulers x 32 lanes
+N_SM = 152
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_ising_L32_h16_m4.txt")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1305_5615_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    kv = {}
+    for line in open(PROFILE_SUMMARY):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except Exception:
+            return {}
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for i, n in enumerate(names):
+                    if r[5 + i].lower().startswith("active"):
+                        reasons.add(n)
+            except (IndexError, ValueError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_rate(wl, seed, seconds):
+    """Single-threaded oracle attempts/s on the same workload, for about
+    `seconds` of CPU work (whole exchange blocks; entry walk excluded)."""
+    from oracle import OracleREWL
+
+    O = OracleREWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seed, q=wl["q"],
+                   sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
+    n_walk = wl["h"] * wl["m"]
+    t0 = time.perf_counter()
+    blocks = 0
+    while True:
+        O.run_blocks(1)
+        blocks += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    attempts = blocks * SPE * wl["L"] ** 2 * n_walk
+    return attempts / el, blocks, el
+
+
+def run_reference(args, wl, world, rank):
+    """The reference arm: the plain CPU oracle on the machine's host cores."""
+    if rank != 0:
+        return
+    from oracle import OracleREWL
+
+    O = OracleREWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], 0, q=wl["q"],
+                   sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
+    per_step = SPE * wl["L"] ** 2 * wl["h"] * wl["m"]
+    for _ in range(args.warmup):
+        O.run_blocks(1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.run_blocks(1)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * per_step / tot
+    sample = ("%d blocks of %d sweeps of the %s workload (%d walkers x %d sites) per step = 1/%d of a "
+              "flatness period" % (1, SPE, args.workload, wl["h"] * wl["m"], wl["L"] ** 2, SPF // SPE))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "step": "one exchange block (100 sweeps)"},
+            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args, wl, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    rewl.load()
+    seed = args.seed + rank
+    stream = torch.cuda.Stream()
+    mode = rewl.MODE_GRAPH if args.mode == "graph" else rewl.MODE_PLAIN
+
+    def make():
+        return rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seed, q=wl["q"],
+                         sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF, stream=stream, profile=True, mode=mode)
+
+    D = make()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        D.step(SPF)
+    i0 = dict(D.info)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)          # L2 flush between timed steps (not inside the events)
+        ev[k][0].record(stream)
+        D.step(SPF)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    i1 = dict(D.info)
+    t_local = sum(step_ms) / 1e3
+    att_local = i1["attempts"] - i0["attempts"]
+    launches = i1["sweep_launches"] - i0["sweep_launches"]
+    sweep_ms = i1["sweep_ms"] - i0["sweep_ms"]
+    t_max, att_sum = t_local, att_local
+    if world > 1:
+        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
+        aa = torch.tensor([att_local], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.all_reduce(aa, op=dist.ReduceOp.SUM)
+        t_max, att_sum = float(tt.item()), float(aa.item())
+    value = att_sum / t_max
+
+    # ---- end to end through the C ABI with host buffers: create (H2D of the
+    # problem), one flatness period, the joined ln g read back (D2H), destroy
+    e2e_times, h2d, d2h, e2e_att = [], [], [], 0
+    for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        E = make()
+        E.step(SPF)
+        g, e0, de = E.lng()
+        inf = dict(E.info)
+        E.close()
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        h2d.append(inf["h2d_bytes"])
+        d2h.append(inf["d2h_bytes"])
+        e2e_att += inf["attempts"]
+    e2e = None
+    if e2e_times:
+        e2e = {"value": e2e_att / sum(e2e_times), "unit": "attempts/s",
+               "h2d_bytes_per_step": int(statistics.mean(h2d)), "d2h_bytes_per_step": int(statistics.mean(d2h)),
+               "step": "rewl_create + rewl_step(1000 sweeps) + rewl_get_lng + rewl_destroy, host buffers"}
+
+    # ---- roofline of the dominant kernel (the sweep kernel)
+    peaks = measured_peaks()
+    f_max = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    roof = None
+    if launches > 0:
+        att_per_launch = att_local / launches
+        avg_s = sweep_ms / launches / 1e3
+        achieved = att_per_launch * OPS_PER_ATTEMPT / avg_s / 1e12
+        peak = N_SM * LANES_PER_SM_PER_CLK * f_max / 1e12
+        traffic = traffic_from_profile()
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_sweep", "avg_launch_ms": avg_s * 1e3,
+                "attempts_per_launch": att_per_launch, "ops_per_attempt": OPS_PER_ATTEMPT,
+                "peak_basis": "152 SMs x 128 int lanes/clk x %.0f MHz (derived, see DESIGN.md)" % (f_max / 1e6),
+                "sweep_share_of_step": sweep_ms / 1e3 / t_local if t_local > 0 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        rate, blocks, el = oracle_rate(wl, seed, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+               "sample": "%d exchange blocks (%d sweeps) of the same workload, %.1f s, entry walk excluded"
+                         % (blocks, blocks * SPE, el)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "desc": wl["desc"], "mode": args.mode,
+                           "lanes_per_walker": i1["lanes_per_walker"], "walkers_per_block": i1["walkers_per_block"],
+                           "step": "one flatness period: 10 x (100 sweeps + exchange) + flatness/merge",
+                           "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                           "parallelism": "replicas x%d (independent seeds)" % world},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps * (3 * (SPF // SPE) + 1), "clocks": clocks,
+                "solve_state": {"sweep_clock": i1["sweep_clock"], "windows_done": i1["windows_done"]}}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="plain", choices=["plain", "graph"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    wl = WORKLOADS[args.workload]
+    world, rank, local = dist_setup()
+    if world > 1 and args.impl == "gb300":
+        import torch.distributed as dist
+        import torch
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, wl, world, rank)
+    else:
+        run_gb300(args, wl, world, rank, local)
+    if world > 1 and args.impl == "gb300":
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

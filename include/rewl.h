@@ -1,0 +1,247 @@
+/*
+ * rewl.h -- C ABI of a GB300 (sm_103a) library for replica-exchange
+ * Wang-Landau (REWL) sampling of 2D lattice spin models, after Vogel, Li,
+ * Wuest, Landau, "A generic, hierarchical framework for massively parallel
+ * Wang-Landau sampling", PRL 110, 210603 (2013).
+ *
+ * The method (paper, WL paragraph, Fig. 1, Eq. (1) and the paragraph after
+ * it): the energy range is split into h overlapping windows; each window
+ * holds m independent Wang-Landau walkers with their own ln g(E) and H(E);
+ * walkers accept single-site moves with min[1, g(E_old)/g(E_new)], add
+ * ln f to ln g and 1 to H at their energy after every trial; walkers of
+ * neighbouring windows swap configurations with probability Eq. (1); when
+ * every walker of a window has a flat H, the window's m ln g tables are
+ * averaged and handed back, H is reset and ln f is halved; the run ends when
+ * every window has reached ln f_final, and the fragments are joined where
+ * d ln g / dE of neighbouring windows agree best.
+ *
+ * Conventions of every call:
+ *  - every call returns a rewl_status; no exception crosses the ABI;
+ *  - out-parameters are written only on REWL_OK;
+ *  - all buffers passed in are HOST memory owned by the caller; the library
+ *    owns all device memory of a handle (allocated with cudaMalloc, or with
+ *    the caller's rewl_params.alloc hook) and frees it in rewl_destroy;
+ *  - a handle is used by one host thread at a time;
+ *  - inputs are copied at creation; the library keeps no caller pointer.
+ *  - rewl_last_error() gives a one-line description of the last failure of
+ *    the calling thread.
+ */
+#ifndef REWL_H
+#define REWL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rewl_ctx* rewl_handle;
+
+typedef enum {
+  REWL_OK = 0,
+  REWL_EINVAL = 1,     /* invalid argument (see rewl_last_error) */
+  REWL_ENOMEM = 2,     /* device or host allocation failed */
+  REWL_ECUDA = 3,      /* a CUDA runtime call failed */
+  REWL_ETIMEOUT = 4,   /* rewl_params.timeout_ms elapsed before done */
+  REWL_EENTRY = 5,     /* a walker could not reach its energy window */
+  REWL_EOVERFLOW = 6,  /* a histogram counter would overflow */
+  REWL_EBUSY = 7,      /* server: no capacity (request stays queued) */
+  REWL_ENOTFOUND = 8,  /* server: unknown request id */
+  REWL_ENODEV = 9      /* no CUDA device, or the device is not sm_103 */
+} rewl_status;
+
+typedef enum { REWL_ISING = 0, REWL_POTTS = 1, REWL_EA_PM_J = 2 } rewl_model_kind;
+
+/* Model: kind; q = number of Potts states (2..16), ignored otherwise.
+ * Ising: E = -sum_<ij> s_i s_j; +-J: E = -sum_<ij> J_ij s_i s_j with
+ * J_ij = +-1; Potts: E = -sum_<ij> delta(s_i, s_j).  The sum runs over the
+ * 2N nearest-neighbour bonds of the periodic square lattice. */
+typedef struct {
+  int32_t kind;
+  int32_t q;
+} rewl_model;
+
+/* Lattice: dim must be 2, Lx == Ly == L with 2 <= L <= 128 (L even for +-J),
+ * periodic must be 1. */
+typedef struct {
+  int32_t dim, Lx, Ly, periodic;
+} rewl_lattice;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator): returns a
+ * device pointer of at least `bytes` bytes usable on `stream`, or NULL. */
+typedef void* (*rewl_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*rewl_free_fn)(void* ptr, void* stream, void* user);
+
+enum { REWL_MODE_PLAIN = 0, REWL_MODE_GRAPH = 1 };
+
+typedef struct {
+  int32_t sweeps_per_exchange;   /* sweeps between exchange rounds; default 100 */
+  int32_t sweeps_per_flat_check; /* sweeps between flatness checks; default 1000; a multiple of the above */
+  double lnf0;                   /* initial ln f; default 1.0; must be a power of two */
+  int32_t entry_max_sweeps;      /* budget of each greedy walk into a window; default 1000 */
+  int32_t discovery_sweeps;      /* +-J only: zero-temperature descent fixing the energy range; default 200 */
+  int64_t timeout_ms;            /* rewl_step returns REWL_ETIMEOUT after this wall time; 0 = none */
+  void* stream;                  /* cudaStream_t to run on; NULL = a stream owned by the handle */
+  int32_t lanes_per_walker;      /* G lanes cooperate on one walker (1,2,4,8,16,32); 0 = autotune */
+  int32_t walkers_per_block;     /* walkers per CTA of the sweep kernel; 0 = autotune */
+  int32_t mode;                  /* REWL_MODE_PLAIN: one launch per phase; REWL_MODE_GRAPH: the
+                                    phases of one flatness period replayed as a captured CUDA graph */
+  rewl_alloc_fn alloc;           /* NULL = cudaMalloc / cudaFree */
+  rewl_free_fn free;
+  void* alloc_user;
+  int32_t profile;               /* 1 = time every sweep launch with CUDA events on the solve's stream
+                                    (plain mode); read back through rewl_info */
+} rewl_params;
+
+/* Fills *p with the defaults above. */
+void rewl_params_default(rewl_params* p);
+
+/*
+ * rewl_create -- set up one REWL solve on the current CUDA device.
+ * Paper: windows and walkers (Fig. 1a caption and the paragraph after it),
+ * the WL parameters (WL paragraph: f schedule ln f -> ln f/2, f_final).
+ *
+ *  out                 receives the handle (untouched on error)
+ *  model, lattice      see above
+ *  couplings           +-J only: 2N values +-1, site-major, [2*i] the bond
+ *                      from site i = y*L + x to its right neighbour, [2*i+1] to
+ *                      the one below; NULL = drawn with p = 1/2 from `seed`.
+ *                      Must be NULL for Ising and Potts.
+ *  windows             h >= 1 energy windows of equal width
+ *  overlap             o in (0, 1): fraction of a window shared with the next
+ *  walkers_per_window  m >= 1 independent walkers per window
+ *  flatness            in (0, 1]: H is flat when min H >= flatness * mean H
+ *                      over the bins the walker has visited (ln g > 0)
+ *  lnf_final           > 0: a window is done when ln f < lnf_final
+ *  seed                64-bit key of every Philox4x32-10 stream of the solve
+ *  params              NULL = rewl_params_default
+ *
+ * Energy bins: Ising [-2N, 2N] step 4; Potts [-2N, 0] step 1; +-J step 4
+ * over [E0, -E0], E0 the lowest energy a zero-temperature descent of all
+ * walkers reaches (g(E) = g(-E) on the bipartite torus).  Windows: w =
+ * ceil(B / (1 + (h-1)(1-o))) bins, window k starts at k(B-w)/(h-1) rounded
+ * half up.  Each walker walks greedily into its window (REWL_EENTRY if it
+ * cannot within the budget, also after a restart from the ground state or,
+ * for +-J, from the lowest configuration found).
+ * Errors: REWL_EINVAL (arguments), REWL_ENOMEM, REWL_ECUDA, REWL_ENODEV,
+ * REWL_EENTRY.
+ */
+rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_lattice* lattice,
+                        const int8_t* couplings, int32_t windows, double overlap, int32_t walkers_per_window,
+                        double flatness, double lnf_final, uint64_t seed, const rewl_params* params);
+
+/*
+ * rewl_step -- advance the solve.  Paper: WL walk (WL paragraph), exchange
+ * (Eq. (1)), flatness / merge / f-reduction and termination (paragraph
+ * after Eq. (1)).  Runs blocks of sweeps_per_exchange sweeps (one sweep =
+ * N trial moves per walker), each followed by one exchange round and, every
+ * sweeps_per_flat_check sweeps, by the flatness check, until at least
+ * max_sweeps sweeps ran or every window is done.  max_sweeps <= 0 runs to
+ * completion.  *done (may be NULL) = 1 when every window reached lnf_final.
+ * Errors: REWL_EINVAL (NULL handle), REWL_ECUDA, REWL_ETIMEOUT (state stays
+ * consistent; call again to continue), REWL_EOVERFLOW.
+ */
+rewl_status rewl_step(rewl_handle h, int64_t max_sweeps, int32_t* done);
+
+/*
+ * rewl_get_lng -- the joined, normalised ln g over the whole energy range
+ * (paper, paragraph after Eq. (1): fragments are joined where the inverse
+ * microcanonical temperatures d ln g/dE agree best).  Each window
+ * contributes the mean of its walkers' ln g; window a+1 is shifted to match
+ * window a at the overlap bin with the smallest difference of central
+ * differences.  Normalised so that sum_E g(E) = 2^N (Ising, +-J) or q^N.
+ *  lng       caller buffer of `capacity` doubles; bin b is energy
+ *            e_min + b * e_step; bins never visited are -INFINITY
+ *  n_bins, e_min, e_step  out (may be NULL)
+ * Errors: REWL_EINVAL (capacity < number of bins, or no visited bin shared
+ * by two neighbouring windows), REWL_ECUDA.
+ */
+rewl_status rewl_get_lng(rewl_handle h, double* lng, int32_t capacity, int32_t* n_bins, int32_t* e_min,
+                         int32_t* e_step);
+
+/*
+ * rewl_get_window_lng -- raw ln g of one walker (walker in [0, m)) of one
+ * window (or, with walker = -1, the mean over the window's walkers), w
+ * values; local bin b is global bin bin_lo + b.  0 = never visited.
+ * Errors: REWL_EINVAL (index or capacity), REWL_ECUDA.
+ */
+rewl_status rewl_get_window_lng(rewl_handle h, int32_t window, int32_t walker, double* lng, int32_t capacity,
+                                int32_t* bin_lo, int32_t* n);
+
+/* Sizes and counters of a solve. */
+typedef struct {
+  int32_t model, q, L, N;
+  int32_t windows, walkers_per_window, window_bins, n_bins;
+  int32_t e_min, e_max, e_step;
+  int32_t lattice_words;     /* 32-bit words per walker configuration */
+  int32_t lanes_per_walker, walkers_per_block, mode, windows_done;
+  int64_t sweep_clock;       /* sweeps done by the solve (all active walkers) */
+  int64_t exchange_rounds;
+  int64_t attempts;          /* WL trial moves done by all walkers (entry walks excluded) */
+  int64_t sweep_launches;    /* sweep-kernel launches timed (params.profile = 1) */
+  double sweep_ms;           /* their summed device time, CUDA events on the solve's stream */
+  int64_t h2d_bytes;         /* bytes copied host -> device by this handle so far */
+  int64_t d2h_bytes;         /* bytes copied device -> host by this handle so far */
+} rewl_info;
+
+rewl_status rewl_get_info(rewl_handle h, rewl_info* info);
+
+/*
+ * Full state of a solve, for parity checks and checkpoint / resume.  Every
+ * pointer is a caller-owned host buffer or NULL (skipped).  Walker W = a*m+k
+ * is walker k of window a.
+ *  lattice   [walkers][lattice_words] u32: Ising/+-J 1 bit per site, row y
+ *            in words [y*Wr, (y+1)*Wr), Wr = ceil(L/32), site (x,y) = bit
+ *            x%32 of word x/32 (bit 1 = spin -1); Potts 4 bits per site,
+ *            Wr = ceil(L/8), site (x,y) = bits 4(x%8).. of word x/8
+ *  E         [walkers] i32 current energy
+ *  lng, H    [walkers][window_bins] f64 / u32, window-local bins
+ *  win_start [windows] first global bin; lnf [windows]; iteration, done
+ *  wl_accept, near_ties, exact_tests [walkers] u64: accepted WL moves;
+ *            acceptance tests with |ln u - Delta ln g| < 1e-12; tests that
+ *            needed the FP64 logarithm
+ *  x_tried, x_accepted [windows] u64: exchange pairs of window pair (a,a+1)
+ */
+typedef struct {
+  uint32_t* lattice;
+  int32_t* E;
+  double* lng;
+  uint32_t* H;
+  int32_t* win_start;
+  double* lnf;
+  int32_t* iteration;
+  int32_t* done;
+  uint64_t* wl_accept;
+  uint64_t* near_ties;
+  uint64_t* exact_tests;
+  uint64_t* x_tried;
+  uint64_t* x_accepted;
+  int64_t sweep_clock;
+  int64_t exchange_rounds;
+} rewl_state;
+
+/* Copies the device state into the caller's buffers.  Errors: REWL_EINVAL,
+ * REWL_ECUDA. */
+rewl_status rewl_get_state(rewl_handle h, rewl_state* st);
+
+/* Restores a state previously read from a handle created with the same
+ * arguments (checkpoint / resume); lattice, E, lng, H, lnf, iteration, done
+ * are required, counters optional.  Because every draw is a function of
+ * (seed, walker, attempt index), a resumed run continues bit-identically.
+ * Errors: REWL_EINVAL, REWL_ECUDA. */
+rewl_status rewl_set_state(rewl_handle h, const rewl_state* st);
+
+/* Frees all device and host memory of the handle.  NULL-safe. */
+void rewl_destroy(rewl_handle h);
+
+/* Static description of a status code. */
+const char* rewl_status_str(rewl_status s);
+
+/* One-line description of the last failure in the calling thread. */
+const char* rewl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REWL_H */

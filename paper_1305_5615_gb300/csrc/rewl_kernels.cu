@@ -1,0 +1,887 @@
+// rewl_kernels.cu -- the device phases of replica-exchange Wang-Landau:
+//   k_init_lattice  random start configurations and their energies
+//   k_descent       +-J: zero-temperature descent that fixes the energy range
+//   k_entry         greedy walk of every walker into its window
+//   k_sweep         the WL walk (paper, WL paragraph) -- the hot loop
+//   k_exchange      configuration swaps between neighbouring windows, Eq. (1)
+//   k_flat_merge    per-walker flatness, averaging of the window's ln g,
+//                   f -> sqrt f and termination (paragraph after Eq. (1))
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "rewl_device.cuh"
+#include "rewl_kernels.h"
+#include "rewl_layout.h"
+
+namespace rewl {
+
+// ---------------------------------------------------------------------------
+// Generic single-site helpers on a walker's packed configuration in global
+// memory (used by the one-off set-up kernels).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t g_site(const Problem& P, const uint32_t* lat, int x, int y) {
+  if (P.model == kPotts) return (lat[y * P.Wr + (x >> 3)] >> ((x & 7) * 4)) & 15u;
+  return (lat[y * P.Wr + (x >> 5)] >> (x & 31)) & 1u;
+}
+__device__ __forceinline__ void g_set_site(const Problem& P, uint32_t* lat, int x, int y, uint32_t v) {
+  if (P.model == kPotts) {
+    uint32_t& wd = lat[y * P.Wr + (x >> 3)];
+    const int sh = (x & 7) * 4;
+    wd = (wd & ~(15u << sh)) | (v << sh);
+  } else {
+    uint32_t& wd = lat[y * P.Wr + (x >> 5)];
+    wd = (wd & ~(1u << (x & 31))) | (v << (x & 31));
+  }
+}
+// bond energy: Ising / +-J -J s_a s_b (bit 1 = spin -1, coupling bit 1 = J -1); Potts -delta
+__device__ __forceinline__ int bond_e(const Problem& P, uint32_t a, uint32_t b, uint32_t jneg) {
+  if (P.model == kPotts) return a == b ? -1 : 0;
+  return ((a ^ b ^ jneg) & 1u) ? 1 : -1;
+}
+__device__ __forceinline__ uint32_t g_jbit(const Problem& P, const uint32_t* J, int plane, int x, int y) {
+  if (P.model != kEA) return 0u;
+  return coupling_bit(J, P.Wr1, plane, P.L, x, y);
+}
+__device__ int g_energy(const Problem& P, const uint32_t* lat, const uint32_t* J) {
+  int E = 0;
+  for (int y = 0; y < P.L; ++y)
+    for (int x = 0; x < P.L; ++x) {
+      const uint32_t s = g_site(P, lat, x, y);
+      const int xr = x + 1 == P.L ? 0 : x + 1, yd = y + 1 == P.L ? 0 : y + 1;
+      E += bond_e(P, s, g_site(P, lat, xr, y), g_jbit(P, J, 0, x, y));
+      E += bond_e(P, s, g_site(P, lat, x, yd), g_jbit(P, J, 1, x, y));
+    }
+  return E;
+}
+__device__ int g_delta_e(const Problem& P, const uint32_t* lat, const uint32_t* J, int x, int y, uint32_t v) {
+  const int L = P.L;
+  const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
+  const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
+  const uint32_t s = g_site(P, lat, x, y);
+  const uint32_t nr = g_site(P, lat, xr, y), nl = g_site(P, lat, xl, y);
+  const uint32_t nd = g_site(P, lat, x, yd), nu = g_site(P, lat, x, yu);
+  const uint32_t jr = g_jbit(P, J, 0, x, y), jl = g_jbit(P, J, 0, xl, y);
+  const uint32_t jd = g_jbit(P, J, 1, x, y), ju = g_jbit(P, J, 1, x, yu);
+  const int before = bond_e(P, s, nr, jr) + bond_e(P, s, nl, jl) + bond_e(P, s, nd, jd) + bond_e(P, s, nu, ju);
+  const int after = bond_e(P, v, nr, jr) + bond_e(P, v, nl, jl) + bond_e(P, v, nd, jd) + bond_e(P, v, nu, ju);
+  return after - before;
+}
+
+__device__ __forceinline__ void propose(const Problem& P, const uint32_t* lat, const U4& r, int& x, int& y,
+                                        uint32_t& v) {
+  const uint32_t site = scale32(r.x, (uint32_t)P.N);
+  y = (int)mulhi32(site, P.magic_L);
+  x = (int)site - y * P.L;
+  const uint32_t s = g_site(P, lat, x, y);
+  if (P.model == kPotts) {
+    v = s + 1u + scale32(r.y, (uint32_t)(P.q - 1));
+    if (v >= (uint32_t)P.q) v -= (uint32_t)P.q;
+  } else {
+    v = s ^ 1u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Set-up kernels (one thread per walker)
+// ---------------------------------------------------------------------------
+__global__ void k_init_lattice(Problem P, DevState S) {
+  const int W = blockIdx.x * blockDim.x + threadIdx.x;
+  if (W >= P.n_walkers) return;
+  uint32_t* lat = S.lat + (size_t)W * P.lat_words;
+  for (int i = 0; i < P.lat_words; ++i) lat[i] = 0u;
+  U4 r{0, 0, 0, 0};
+  for (int i = 0; i < P.N; ++i) {
+    const int x = i % P.L, y = i / P.L;
+    if (P.model == kPotts) {
+      if ((i & 3) == 0) r = philox10((uint32_t)(i >> 2), 0u, (uint32_t)W, kTagInit, P.seed_lo, P.seed_hi);
+      const uint32_t w = (i & 3) == 0 ? r.x : (i & 3) == 1 ? r.y : (i & 3) == 2 ? r.z : r.w;
+      g_set_site(P, lat, x, y, scale32(w, (uint32_t)P.q));
+    } else {
+      if ((i & 127) == 0) r = philox10((uint32_t)(i >> 7), 0u, (uint32_t)W, kTagInit, P.seed_lo, P.seed_hi);
+      const int wi = (i & 127) >> 5;
+      const uint32_t w = wi == 0 ? r.x : wi == 1 ? r.y : wi == 2 ? r.z : r.w;
+      g_set_site(P, lat, x, y, (w >> (i & 31)) & 1u);
+    }
+  }
+  S.E[W] = g_energy(P, lat, S.J);
+  S.entry_t[W] = 0;
+  S.status[W] = 0;
+}
+
+__device__ __forceinline__ int window_distance(int E, int lo, int hi) { return E < lo ? lo - E : (E > hi ? E - hi : 0); }
+
+// One greedy move on the entry stream.  target < 0: minimise E (descent);
+// otherwise minimise the distance to window `target`.
+__device__ void greedy_move(const Problem& P, DevState& S, uint32_t* lat, int W, int lo, int hi, bool descent) {
+  const uint64_t t = S.entry_t[W]++;
+  const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagEntry, P.seed_lo, P.seed_hi);
+  int x, y;
+  uint32_t v;
+  propose(P, lat, r, x, y, v);
+  const int E = S.E[W];
+  const int En = E + g_delta_e(P, lat, S.J, x, y, v);
+  const int before = descent ? E : window_distance(E, lo, hi);
+  const int after = descent ? En : window_distance(En, lo, hi);
+  if (after <= before) {
+    g_set_site(P, lat, x, y, v);
+    S.E[W] = En;
+  }
+}
+
+__global__ void k_descent(Problem P, DevState S, uint64_t n_att) {
+  const int W = blockIdx.x * blockDim.x + threadIdx.x;
+  if (W >= P.n_walkers) return;
+  uint32_t* lat = S.lat + (size_t)W * P.lat_words;
+  for (uint64_t n = 0; n < n_att; ++n) greedy_move(P, S, lat, W, 0, 0, true);
+}
+
+__global__ void k_entry(Problem P, DevState S, uint64_t budget) {
+  const int W = blockIdx.x * blockDim.x + threadIdx.x;
+  if (W >= P.n_walkers) return;
+  uint32_t* lat = S.lat + (size_t)W * P.lat_words;
+  const int a = W / P.m;
+  const int lo = P.e_min + S.win_start[a] * P.e_step;
+  const int hi = P.e_min + (S.win_start[a] + P.w - 1) * P.e_step;
+  for (uint64_t n = 0; n < budget && window_distance(S.E[W], lo, hi) > 0; ++n) greedy_move(P, S, lat, W, lo, hi, false);
+  if (window_distance(S.E[W], lo, hi) == 0) return;
+  for (int i = 0; i < P.lat_words; ++i) lat[i] = S.seed_config[i];
+  S.E[W] = g_energy(P, lat, S.J);
+  for (uint64_t n = 0; n < budget && window_distance(S.E[W], lo, hi) > 0; ++n) greedy_move(P, S, lat, W, lo, hi, false);
+  if (window_distance(S.E[W], lo, hi) != 0) S.status[W] = 5;  // REWL_EENTRY
+}
+
+// ---------------------------------------------------------------------------
+// The WL sweep kernel.
+//
+// G lanes run one walker.  For every group of G consecutive trials each lane
+// draws one trial (Philox, site, proposed Potts value, float log of u) in
+// parallel; the G trials are then applied in order, every lane of the group
+// executing the same (redundant) sequential step.  The walker's
+// configuration, the fixed-point shadow of its ln g (units of 2^-40) and its
+// H live in shared memory, interleaved by walker.  The acceptance test
+//      accept iff ln g(E_old) - ln g(E_new) >= ln u         (min[1, g_old/g_new])
+// is decided on the shadow against float ln u whenever the two differ by more
+// than the guard band; otherwise (rarely) it is recomputed exactly in FP64
+// from the stored doubles, as the plain definition does.  The FP64 ln g is
+// brought up to date at the end of the launch by exact integer emulation of
+// the per-visit additions ln g += ln f (add_pow2_repeated), so the hot loop
+// issues no FP64 instruction.
+// ---------------------------------------------------------------------------
+template <int G>
+__device__ __forceinline__ uint32_t group_mask() {
+  if (G == 32) return 0xffffffffu;
+  const uint32_t lane = threadIdx.x & 31u;
+  return ((1u << G) - 1u) << (lane & ~(uint32_t)(G - 1));
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T gshfl(uint32_t mask, T v, int src) {
+  if constexpr (G == 1) {
+    return v;
+  } else if constexpr (sizeof(T) == 8) {
+    const long long b = __shfl_sync(mask, (long long)v, src, G);
+    return (T)b;
+  } else {
+    return __shfl_sync(mask, v, src, G);
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void gsync(uint32_t mask) {
+  if constexpr (G > 1) __syncwarp(mask);
+}
+
+// exact FP64 re-evaluation of one acceptance test (rare)
+__device__ __noinline__ bool exact_accept(const DevState& S, const Problem& P, int W, int k, int bin, uint32_t h_cur,
+                                          int bn, uint32_t h_new, uint64_t k52, uint64_t& n_tie) {
+  const double* lngW = S.lng + (size_t)W * P.w;
+  const uint32_t* HW = S.H + (size_t)W * P.w;
+  const uint64_t vc = add_pow2_repeated(double_to_bits(lngW[bin]), k, h_cur - HW[bin]);
+  const uint64_t vn = add_pow2_repeated(double_to_bits(lngW[bn]), k, h_new - HW[bn]);
+  const double delta = __dsub_rn(bits_to_double(vc), bits_to_double(vn));
+  if (delta >= 0.0) return true;
+  const double u = __dmul_rn(__ull2double_rn(2ull * k52 + 1ull), 0x1p-53);
+  const double lu = log(u);
+  if (fabs(__dsub_rn(lu, delta)) < 1e-12) ++n_tie;
+  return lu < delta;
+}
+
+template <int MODEL, int G>
+__global__ void __launch_bounds__(256) k_sweep(Problem P, DevState S, SweepLaunch A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wpb = A.wpb;
+  int64_t* s_fx = reinterpret_cast<int64_t*>(smem);
+  uint32_t* s_H = reinterpret_cast<uint32_t*>(s_fx + (size_t)P.w * wpb);
+  uint32_t* s_lat = s_H + (size_t)P.w * wpb;
+  uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  const int first = blockIdx.x * wpb;
+  const int nloc = min(wpb, A.n_active - first);
+
+  // ---- stage the walkers of this CTA into shared memory
+  for (int i = tid; i < nloc * P.w; i += nthr) {
+    const int l = i / P.w, b = i - l * P.w;
+    const size_t g = (size_t)S.active[first + l] * P.w + b;
+    s_fx[b * wpb + l] = to_fx(double_to_bits(S.lng[g]));
+    s_H[b * wpb + l] = S.H[g];
+  }
+  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
+    const int l = i / P.lat_words, j = i - l * P.lat_words;
+    s_lat[j * wpb + l] = S.lat[(size_t)S.active[first + l] * P.lat_words + j];
+  }
+  if (MODEL == kEA)
+    for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
+  __syncthreads();
+
+  const int lw = tid / G, lane = tid % G;
+  bool valid = lw < nloc;
+  int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
+  if (valid) {
+    W = S.active[first + lw];
+    a = W / P.m;
+    wstart = S.win_start[a];
+    bin = (S.E[W] - P.e_min) / P.e_step - wstart;
+    if ((unsigned)bin >= (unsigned)P.w) {  // cannot happen for a consistent state; never index with it
+      if (lane == 0) S.status[W] = 6;
+      valid = false;
+    }
+  }
+  if (valid) {
+    kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);  // ln f = 2^-kexp
+    const int64_t lnf_fx = kexp <= kFxBits ? (1ll << (kFxBits - kexp)) : 0;
+    int64_t fx_cur = s_fx[bin * wpb + lw];
+    uint32_t h_cur = s_H[bin * wpb + lw];
+    uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
+    const uint32_t gm = group_mask<G>();
+    const int L = P.L, Wr = P.Wr, w = P.w;
+    const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
+
+    for (uint32_t base = 0; base < A.n_att; base += G) {
+      // -- parallel part: lane draws trial base + lane
+      const uint64_t t = t0 + base + (uint32_t)lane;
+      const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+      const uint32_t site = scale32(r.x, (uint32_t)P.N);
+      const uint32_t yy = mulhi32(site, P.magic_L);
+      const uint32_t xx = site - yy * (uint32_t)L;
+      const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+      const uint64_t k52 = u52_bits(r.z, r.w);
+      const float uf = __ull2float_rn(2ull * k52 + 1ull) * 0x1p-53f;
+      const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);  // ln u in units of 2^-40
+      const uint32_t packed = xx | (yy << 8) | (pv << 16);
+
+      // -- sequential part: the G trials in order (fewer in the last group
+      //    when the launch's trial count is not a multiple of G)
+      const int n_here = (int)min((uint32_t)G, A.n_att - base);
+#pragma unroll 1
+      for (int j = 0; j < n_here; ++j) {
+        const uint32_t pk = gshfl<G>(gm, packed, j);
+        const int64_t th = gshfl<G>(gm, thr, j);
+        gsync<G>(gm);  // previous trial's stores are visible to the whole group
+        const int x = pk & 0xff, y = (pk >> 8) & 0xff;
+        const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
+        const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
+        int dbin;
+        uint32_t word_idx, new_word;
+        if constexpr (MODEL == kPotts) {
+          const uint32_t v = potts_val(s_lat, wpb, lw, Wr, x, y);
+          uint32_t nv = v + 1u + (pk >> 16);
+          if (nv >= (uint32_t)P.q) nv -= (uint32_t)P.q;
+          const uint32_t n1 = potts_val(s_lat, wpb, lw, Wr, xr, y), n2 = potts_val(s_lat, wpb, lw, Wr, xl, y);
+          const uint32_t n3 = potts_val(s_lat, wpb, lw, Wr, x, yd), n4 = potts_val(s_lat, wpb, lw, Wr, x, yu);
+          dbin = (int)(n1 == v) + (int)(n2 == v) + (int)(n3 == v) + (int)(n4 == v) - (int)(n1 == nv) -
+                 (int)(n2 == nv) - (int)(n3 == nv) - (int)(n4 == nv);
+          word_idx = (uint32_t)((y * Wr + (x >> 3)) * wpb + lw);
+          const int sh = (x & 7) * 4;
+          new_word = (s_lat[word_idx] & ~(15u << sh)) | (nv << sh);
+        } else {
+          const uint32_t c = spin_bit(s_lat, wpb, lw, Wr, x, y);
+          const uint32_t nr = spin_bit(s_lat, wpb, lw, Wr, xr, y), nl = spin_bit(s_lat, wpb, lw, Wr, xl, y);
+          const uint32_t nd = spin_bit(s_lat, wpb, lw, Wr, x, yd), nu = spin_bit(s_lat, wpb, lw, Wr, x, yu);
+          uint32_t jr = 0, jl = 0, jd = 0, ju = 0;
+          if constexpr (MODEL == kEA) {
+            jr = coupling_bit(s_J, P.Wr1, 0, L, x, y);
+            jl = coupling_bit(s_J, P.Wr1, 0, L, xl, y);
+            jd = coupling_bit(s_J, P.Wr1, 1, L, x, y);
+            ju = coupling_bit(s_J, P.Wr1, 1, L, x, yu);
+          }
+          // bond satisfied iff J s s' = +1 iff (b ^ b' ^ jneg) == 0; dE = 4 * satisfied - 8
+          const int sat = (int)(((c ^ nr ^ jr) & 1u) == 0) + (int)(((c ^ nl ^ jl) & 1u) == 0) +
+                          (int)(((c ^ nd ^ jd) & 1u) == 0) + (int)(((c ^ nu ^ ju) & 1u) == 0);
+          dbin = sat - 2;
+          word_idx = (uint32_t)((y * Wr + (x >> 5)) * wpb + lw);
+          new_word = s_lat[word_idx] ^ (1u << (x & 31));
+        }
+        const int bn = bin + dbin;
+        bool acc;
+        int64_t fxn = fx_cur;
+        uint32_t hn = h_cur;
+        if (dbin == 0) {
+          acc = true;  // ln g(E_old) - ln g(E_new) = 0
+        } else if ((unsigned)bn >= (unsigned)w) {
+          acc = false;  // the move leaves the window
+        } else {
+          fxn = s_fx[bn * wpb + lw];
+          hn = s_H[bn * wpb + lw];
+          const int64_t d = (fx_cur - fxn) - th;
+          if (d > kGuardFx) {
+            acc = true;
+          } else if (d < -kGuardFx) {
+            acc = false;
+          } else {
+            const uint32_t r2 = gshfl<G>(gm, r.z, j), r3 = gshfl<G>(gm, r.w, j);
+            acc = exact_accept(S, P, W, kexp, bin, h_cur, bn, hn, u52_bits(r2, r3), n_tie);
+            ++n_exact;
+          }
+        }
+        gsync<G>(gm);  // all reads of this trial precede its stores
+        if (acc) {
+          if (lane == 0) s_lat[word_idx] = new_word;
+          if (dbin != 0) {
+            if (lane == 0) {
+              s_fx[bin * wpb + lw] = fx_cur;
+              s_H[bin * wpb + lw] = h_cur;
+            }
+            bin = bn;
+            fx_cur = fxn;
+            h_cur = hn;
+          }
+          ++n_acc;
+        }
+        fx_cur += lnf_fx;  // ln g(E) += ln f on the shadow
+        ++h_cur;           // H(E) += 1
+      }
+    }
+    gsync<G>(gm);
+    if (lane == 0) {
+      s_fx[bin * wpb + lw] = fx_cur;
+      s_H[bin * wpb + lw] = h_cur;
+      S.E[W] = P.e_min + (wstart + bin) * P.e_step;
+      S.wl_accept[W] += n_acc;
+      S.near_ties[W] += n_tie;
+      S.exact_tests[W] += n_exact;
+    }
+  }
+  __syncthreads();
+
+  // ---- write back: exact FP64 ln g from the visit counts of this launch
+  for (int i = tid; i < nloc * P.w; i += nthr) {
+    const int l = i / P.w, b = i - l * P.w;
+    const int Wl = S.active[first + l];
+    const size_t g = (size_t)Wl * P.w + b;
+    const uint32_t hs = s_H[b * wpb + l];
+    const uint32_t c = hs - S.H[g];
+    if (c) {
+      const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
+      S.lng[g] = bits_to_double(add_pow2_repeated(double_to_bits(S.lng[g]), kx, c));
+      S.H[g] = hs;
+    }
+  }
+  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
+    const int l = i / P.lat_words, j = i - l * P.lat_words;
+    S.lat[(size_t)S.active[first + l] * P.lat_words + j] = s_lat[j * wpb + l];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The WL sweep kernel, speculative form (G = 8, 16 or 32 lanes per walker).
+//
+// Same trials, same order, same results as k_sweep; only the work is split
+// differently.  For a group of G consecutive trials every lane evaluates its
+// own trial against the configuration as it stands when the group starts:
+// the Philox draw, the site, the proposed value, the energy change (as a bin
+// offset) and ln u.  It also records which earlier trials of the group touch
+// its site or a neighbour (mask M_j).  The trials are then applied in order;
+// a trial whose mask meets an earlier *accepted* trial is re-evaluated on the
+// current configuration, all others use the speculative offset.  What stays
+// sequential is the chain bin -> ln g shadow of the new bin -> acceptance.
+// ---------------------------------------------------------------------------
+template <int MODEL>
+struct TrialEval {
+  int dbin;          // (E_new - E_old) / e_step
+  uint32_t widx;     // lattice word (shared-memory index) the move writes
+  uint32_t wmask;    // Ising / +-J: bit to flip;  Potts: nibble shift (low 8 bits) | new value << 8
+};
+
+template <int MODEL>
+__device__ __forceinline__ TrialEval<MODEL> eval_trial(const Problem& P, const uint32_t* s_lat, const uint32_t* s_J,
+                                                       int wpb, int lw, int x, int y, uint32_t pv) {
+  const int L = P.L, Wr = P.Wr;
+  const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
+  const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
+  TrialEval<MODEL> t;
+  if constexpr (MODEL == kPotts) {
+    const uint32_t v = potts_val(s_lat, wpb, lw, Wr, x, y);
+    uint32_t nv = v + 1u + pv;
+    if (nv >= (uint32_t)P.q) nv -= (uint32_t)P.q;
+    const uint32_t n1 = potts_val(s_lat, wpb, lw, Wr, xr, y), n2 = potts_val(s_lat, wpb, lw, Wr, xl, y);
+    const uint32_t n3 = potts_val(s_lat, wpb, lw, Wr, x, yd), n4 = potts_val(s_lat, wpb, lw, Wr, x, yu);
+    t.dbin = (int)(n1 == v) + (int)(n2 == v) + (int)(n3 == v) + (int)(n4 == v) - (int)(n1 == nv) - (int)(n2 == nv) -
+             (int)(n3 == nv) - (int)(n4 == nv);
+    t.widx = (uint32_t)((y * Wr + (x >> 3)) * wpb + lw);
+    t.wmask = (uint32_t)((x & 7) * 4) | (nv << 8);
+  } else {
+    const uint32_t c = spin_bit(s_lat, wpb, lw, Wr, x, y);
+    const uint32_t nr = spin_bit(s_lat, wpb, lw, Wr, xr, y), nl = spin_bit(s_lat, wpb, lw, Wr, xl, y);
+    const uint32_t nd = spin_bit(s_lat, wpb, lw, Wr, x, yd), nu = spin_bit(s_lat, wpb, lw, Wr, x, yu);
+    uint32_t jr = 0, jl = 0, jd = 0, ju = 0;
+    if constexpr (MODEL == kEA) {
+      jr = coupling_bit(s_J, P.Wr1, 0, L, x, y);
+      jl = coupling_bit(s_J, P.Wr1, 0, L, xl, y);
+      jd = coupling_bit(s_J, P.Wr1, 1, L, x, y);
+      ju = coupling_bit(s_J, P.Wr1, 1, L, x, yu);
+    }
+    const int sat = (int)(((c ^ nr ^ jr) & 1u) == 0) + (int)(((c ^ nl ^ jl) & 1u) == 0) +
+                    (int)(((c ^ nd ^ jd) & 1u) == 0) + (int)(((c ^ nu ^ ju) & 1u) == 0);
+    t.dbin = sat - 2;  // dE = 4 * satisfied - 8
+    t.widx = (uint32_t)((y * Wr + (x >> 5)) * wpb + lw);
+    t.wmask = 1u << (x & 31);
+  }
+  return t;
+}
+
+template <int MODEL>
+__device__ __forceinline__ void apply_move(uint32_t* s_lat, uint32_t widx, uint32_t wmask) {
+  if constexpr (MODEL == kPotts) {
+    const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
+    s_lat[widx] = (s_lat[widx] & ~(15u << sh)) | (nv << sh);
+  } else {
+    s_lat[widx] ^= wmask;
+  }
+}
+
+// One staged trial: what the parallel phase hands to the sequential phase.
+struct StagedTrial {
+  uint32_t pk;     // dbin + 8 | pv << 8 | x << 16 | y << 24
+  uint32_t mask;   // earlier trials of the group whose site lies in this trial's 5-site neighbourhood
+  uint32_t widx;   // lattice word the move writes (shared-memory index)
+  uint32_t wmask;  // Ising / +-J: bit to flip;  Potts: nibble shift | new value << 8
+  int64_t thr;     // ln u in units of 2^-40 (float log; see kGuardFx)
+};
+
+template <int MODEL, int G>
+__global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, SweepLaunch A) {
+  static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wpb = A.wpb;
+  StagedTrial* s_stage = reinterpret_cast<StagedTrial*>(smem);                 // [wpb][G]
+  int64_t* s_fx = reinterpret_cast<int64_t*>(s_stage + (G > 1 ? (size_t)wpb * G : 0));
+  uint32_t* s_H = reinterpret_cast<uint32_t*>(s_fx + (size_t)P.w * wpb);
+  uint32_t* s_lat = s_H + (size_t)P.w * wpb;
+  uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  const int first = blockIdx.x * wpb;
+  const int nloc = min(wpb, A.n_active - first);
+
+  for (int i = tid; i < nloc * P.w; i += nthr) {
+    const int l = i / P.w, b = i - l * P.w;
+    const size_t g = (size_t)S.active[first + l] * P.w + b;
+    s_fx[b * wpb + l] = to_fx(double_to_bits(S.lng[g]));
+    s_H[b * wpb + l] = S.H[g];
+  }
+  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
+    const int l = i / P.lat_words, j = i - l * P.lat_words;
+    s_lat[j * wpb + l] = S.lat[(size_t)S.active[first + l] * P.lat_words + j];
+  }
+  if (MODEL == kEA)
+    for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
+  __syncthreads();
+
+  const int lw = tid / G, lane = tid % G;
+  bool valid = lw < nloc;
+  int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
+  if (valid) {
+    W = S.active[first + lw];
+    a = W / P.m;
+    wstart = S.win_start[a];
+    bin = (S.E[W] - P.e_min) / P.e_step - wstart;
+    if ((unsigned)bin >= (unsigned)P.w) {
+      if (lane == 0) S.status[W] = 6;
+      valid = false;
+    }
+  }
+  if (valid) {
+    kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
+    const int64_t lnf_fx = kexp <= kFxBits ? (1ll << (kFxBits - kexp)) : 0;
+    int64_t fx_cur = s_fx[bin * wpb + lw];
+    uint32_t h_cur = s_H[bin * wpb + lw];
+    uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
+    const uint32_t gm = group_mask<G>();
+    const int L = P.L, w = P.w;
+    const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
+    StagedTrial* my_stage = s_stage + (size_t)lw * G;
+
+    for (uint32_t base = 0; base < A.n_att; base += G) {
+      // ---- parallel phase: lane l evaluates trial base + l on the current configuration
+      StagedTrial tr;
+      {
+        const uint64_t t = t0 + base + (uint32_t)lane;
+        const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+        const uint32_t site = scale32(r.x, (uint32_t)P.N);
+        const int y = (int)mulhi32(site, P.magic_L);
+        const int x = (int)site - y * L;
+        const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+        const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
+        tr.thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
+        const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
+        const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
+        uint32_t M = 0;
+        if constexpr (G > 1) {
+          const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
+          const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
+          const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
+          const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
+#pragma unroll
+          for (int i = 0; i < G - 1; ++i) {
+            const uint32_t pi = __shfl_sync(gm, pk, i, G);
+            const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
+            M |= (hit && i < lane) ? (1u << i) : 0u;
+          }
+        }
+        tr.pk = (uint32_t)(ev.dbin + 8) | (pv << 8) | (pk << 16);
+        tr.mask = M;
+        tr.widx = ev.widx;
+        tr.wmask = ev.wmask;
+        if constexpr (G > 1) my_stage[lane] = tr;
+      }
+      if constexpr (G > 1) __syncwarp(gm);  // staged trials visible to lane 0
+
+      // ---- sequential phase: lane 0 applies the trials in order
+      if (lane == 0) {
+        const int n_here = (int)min((uint32_t)G, A.n_att - base);
+        uint32_t accm = 0;
+        StagedTrial nxt = tr;
+        if constexpr (G > 1) nxt = my_stage[0];
+#pragma unroll 1
+        for (int j = 0; j < n_here; ++j) {
+          const StagedTrial cur = nxt;
+          if constexpr (G > 1) {
+            if (j + 1 < n_here) nxt = my_stage[j + 1];  // prefetch the next staged trial
+          }
+          int dbin = (int)(cur.pk & 0xffu) - 8;
+          uint32_t widx = cur.widx, wmask = cur.wmask;
+          if constexpr (G > 1) {
+            if (accm & cur.mask) {  // an accepted earlier trial touched this neighbourhood: re-evaluate
+              const TrialEval<MODEL> e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cur.pk >> 16) & 0xffu),
+                                                           (int)(cur.pk >> 24), (cur.pk >> 8) & 0xffu);
+              dbin = e2.dbin;
+              widx = e2.widx;
+              wmask = e2.wmask;
+            }
+          }
+          const int bn = bin + dbin;
+          const bool inwin = (unsigned)bn < (unsigned)w;
+          const int bl = inwin ? bn : bin;
+          const int64_t fxn = s_fx[bl * wpb + lw];
+          const int64_t d = (fx_cur - fxn) - cur.thr;
+          bool acc = dbin == 0 || (inwin && d > kGuardFx);
+          if (dbin != 0 && inwin && d >= -kGuardFx && d <= kGuardFx) {
+            const uint64_t t = t0 + base + (uint32_t)j;
+            const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+            acc = exact_accept(S, P, W, kexp, bin, h_cur, bn, s_H[bn * wpb + lw], u52_bits(r.z, r.w), n_tie);
+            ++n_exact;
+          }
+          if (acc) {
+            accm |= 1u << j;
+            apply_move<MODEL>(s_lat, widx, wmask);
+            if (dbin != 0) {
+              s_fx[bin * wpb + lw] = fx_cur;
+              s_H[bin * wpb + lw] = h_cur;
+              bin = bn;
+              fx_cur = fxn;
+              h_cur = s_H[bn * wpb + lw];
+            }
+            ++n_acc;
+          }
+          fx_cur += lnf_fx;  // ln g(E) += ln f on the shadow
+          ++h_cur;           // H(E) += 1
+        }
+      }
+      if constexpr (G > 1) __syncwarp(gm);  // lane 0's configuration updates visible to the group
+    }
+    if (lane == 0) {
+      s_fx[bin * wpb + lw] = fx_cur;
+      s_H[bin * wpb + lw] = h_cur;
+      S.E[W] = P.e_min + (wstart + bin) * P.e_step;
+      S.wl_accept[W] += n_acc;
+      S.near_ties[W] += n_tie;
+      S.exact_tests[W] += n_exact;
+    }
+  }
+  __syncthreads();
+
+  for (int i = tid; i < nloc * P.w; i += nthr) {
+    const int l = i / P.w, b = i - l * P.w;
+    const int Wl = S.active[first + l];
+    const size_t g = (size_t)Wl * P.w + b;
+    const uint32_t hs = s_H[b * wpb + l];
+    const uint32_t c = hs - S.H[g];
+    if (c) {
+      const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
+      S.lng[g] = bits_to_double(add_pow2_repeated(double_to_bits(S.lng[g]), kx, c));
+      S.H[g] = hs;
+    }
+  }
+  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
+    const int l = i / P.lat_words, j = i - l * P.lat_words;
+    S.lat[(size_t)S.active[first + l] * P.lat_words + j] = s_lat[j * wpb + l];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Replica exchange, Eq. (1).  One CTA per window pair (a, a+1), a = round
+// (mod 2); walker k of window a is paired with walker sigma(k) of window a+1,
+// sigma a Fisher-Yates permutation from the round's own stream.
+// ---------------------------------------------------------------------------
+__global__ void k_exchange(Problem P, DevState S) {
+  extern __shared__ int sigma[];
+  const uint32_t round = (uint32_t)S.clock[1];
+  const int a = 2 * (int)blockIdx.x + (int)(round & 1u);
+  if (a + 1 >= P.h) return;
+  if (S.done[a] || S.done[a + 1]) return;
+  const int m = P.m;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < m; ++k) sigma[k] = k;
+    for (int i = m - 1; i >= 1; --i) {
+      const U4 r = philox10(round, (uint32_t)a, (uint32_t)i, kTagPerm, P.seed_lo, P.seed_hi);
+      const int j = (int)scale32(r.x, (uint32_t)(i + 1));
+      const int tmp = sigma[i];
+      sigma[i] = sigma[j];
+      sigma[j] = tmp;
+    }
+  }
+  __syncthreads();
+  const int loA = P.e_min + S.win_start[a] * P.e_step, hiA = loA + (P.w - 1) * P.e_step;
+  const int loB = P.e_min + S.win_start[a + 1] * P.e_step, hiB = loB + (P.w - 1) * P.e_step;
+  unsigned n_acc = 0;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const int Wi = a * m + k, Wj = (a + 1) * m + sigma[k];
+    const int EX = S.E[Wi], EY = S.E[Wj];
+    if (EX < loB || EX > hiB || EY < loA || EY > hiA) continue;
+    const double* gi = S.lng + (size_t)Wi * P.w;
+    const double* gj = S.lng + (size_t)Wj * P.w;
+    const int iX = (EX - loA) / P.e_step, iY = (EY - loA) / P.e_step;
+    const int jX = (EX - loB) / P.e_step, jY = (EY - loB) / P.e_step;
+    const double d1 = __dsub_rn(gi[iX], gi[iY]);
+    const double d2 = __dsub_rn(gj[jY], gj[jX]);
+    const double D = __dadd_rn(d1, d2);
+    bool acc = D >= 0.0;
+    if (!acc) {
+      const U4 r = philox10(round, (uint32_t)a, (uint32_t)k, kTagXacc, P.seed_lo, P.seed_hi);
+      const double u = __dmul_rn(__ull2double_rn(2ull * u52_bits(r.z, r.w) + 1ull), 0x1p-53);
+      const double lu = log(u);
+      if (fabs(__dsub_rn(lu, D)) < 1e-12) S.near_ties[Wi] += 1;
+      acc = lu < D;
+    }
+    if (acc) {
+      uint32_t* li = S.lat + (size_t)Wi * P.lat_words;
+      uint32_t* lj = S.lat + (size_t)Wj * P.lat_words;
+      for (int i = 0; i < P.lat_words; ++i) {
+        const uint32_t t = li[i];
+        li[i] = lj[i];
+        lj[i] = t;
+      }
+      S.E[Wi] = EY;
+      S.E[Wj] = EX;
+      ++n_acc;
+    }
+  }
+  if (n_acc) atomicAdd(reinterpret_cast<unsigned long long*>(&S.x_accepted[a]), (unsigned long long)n_acc);
+  if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&S.x_tried[a]), (unsigned long long)m);
+}
+
+// ---------------------------------------------------------------------------
+// Flatness, merge and f update.  One CTA per window.
+// ---------------------------------------------------------------------------
+__global__ void k_flat_merge(Problem P, DevState S) {
+  const int a = blockIdx.x;
+  if (S.done[a]) return;
+  __shared__ uint32_t r_min[32];
+  __shared__ unsigned long long r_sum[32];
+  __shared__ int r_n[32];
+  __shared__ int all_flat;
+  const int m = P.m, w = P.w;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (threadIdx.x == 0) all_flat = 1;
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    const int W = a * m + k;
+    uint32_t hmin = 0xffffffffu;
+    unsigned long long s = 0;
+    int n = 0;
+    for (int b = threadIdx.x; b < w; b += blockDim.x) {
+      if (S.lng[(size_t)W * w + b] > 0.0) {
+        const uint32_t hv = S.H[(size_t)W * w + b];
+        hmin = min(hmin, hv);
+        s += hv;
+        ++n;
+      }
+    }
+    for (int o = 16; o; o >>= 1) {
+      hmin = min(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      n += __shfl_xor_sync(0xffffffffu, n, o);
+    }
+    if (lane == 0) {
+      r_min[wid] = hmin;
+      r_sum[wid] = s;
+      r_n[wid] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t hm = 0xffffffffu;
+      unsigned long long ss = 0;
+      int nn = 0;
+      for (int i = 0; i < nw; ++i) {
+        hm = min(hm, r_min[i]);
+        ss += r_sum[i];
+        nn += r_n[i];
+      }
+      // flat iff min H * n >= flatness * sum H over the visited bins
+      const bool flat = nn > 0 && __dmul_rn(__uint2double_rn(hm), __int2double_rn(nn)) >=
+                                      __dmul_rn(P.flatness, __ull2double_rn(ss));
+      if (!flat) all_flat = 0;
+    }
+    __syncthreads();
+    if (!all_flat) return;
+  }
+  // merge: mean of the m estimators (summed in walker order), H reset
+  for (int b = threadIdx.x; b < w; b += blockDim.x) {
+    double sum = S.lng[(size_t)(a * m) * w + b];
+    for (int k = 1; k < m; ++k) sum = __dadd_rn(sum, S.lng[(size_t)(a * m + k) * w + b]);
+    const double mean = __ddiv_rn(sum, (double)m);
+    for (int k = 0; k < m; ++k) {
+      S.lng[(size_t)(a * m + k) * w + b] = mean;
+      S.H[(size_t)(a * m + k) * w + b] = 0u;
+    }
+  }
+  if (threadIdx.x == 0) {
+    const double lnf = __dmul_rn(S.lnf[a], 0.5);  // f -> sqrt(f)
+    S.lnf[a] = lnf;
+    S.iter[a] += 1;
+    if (lnf < P.lnf_final) {
+      S.done[a] = 1;
+      atomicAdd(S.n_done, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launch wrappers
+// ---------------------------------------------------------------------------
+// G <= 4 lanes per walker: k_sweep; G >= 8: the speculative k_sweep_spec.
+template <int MODEL, int G>
+static auto sweep_kernel() {
+  return k_sweep_spec<MODEL, G>;
+}
+
+template <int MODEL, int G>
+static cudaError_t prepare_sweep_t() {
+  return cudaFuncSetAttribute(sweep_kernel<MODEL, G>(), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
+template <int MODEL>
+static cudaError_t prepare_sweep_m(int G) {
+  switch (G) {
+    case 1: return prepare_sweep_t<MODEL, 1>();
+    case 2: return prepare_sweep_t<MODEL, 2>();
+    case 4: return prepare_sweep_t<MODEL, 4>();
+    case 8: return prepare_sweep_t<MODEL, 8>();
+    case 16: return prepare_sweep_t<MODEL, 16>();
+    case 32: return prepare_sweep_t<MODEL, 32>();
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Allows the sweep kernel of (model, G) up to 227 KB of dynamic shared memory.
+cudaError_t prepare_sweep(int G, int model) {
+  switch (model) {
+    case kIsing: return prepare_sweep_m<kIsing>(G);
+    case kPotts: return prepare_sweep_m<kPotts>(G);
+    case kEA: return prepare_sweep_m<kEA>(G);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int MODEL, int G>
+static cudaError_t launch_sweep_t(const Problem& P, const DevState& S, const SweepLaunch& A, size_t smem,
+                                  cudaStream_t st) {
+  const int blocks = (A.n_active + A.wpb - 1) / A.wpb;
+  sweep_kernel<MODEL, G>()<<<blocks, A.wpb * G, smem, st>>>(P, S, A);
+  return cudaGetLastError();
+}
+
+template <int MODEL>
+static cudaError_t launch_sweep_m(int G, const Problem& P, const DevState& S, const SweepLaunch& A, size_t smem,
+                                  cudaStream_t st) {
+  switch (G) {
+    case 1: return launch_sweep_t<MODEL, 1>(P, S, A, smem, st);
+    case 2: return launch_sweep_t<MODEL, 2>(P, S, A, smem, st);
+    case 4: return launch_sweep_t<MODEL, 4>(P, S, A, smem, st);
+    case 8: return launch_sweep_t<MODEL, 8>(P, S, A, smem, st);
+    case 16: return launch_sweep_t<MODEL, 16>(P, S, A, smem, st);
+    case 32: return launch_sweep_t<MODEL, 32>(P, S, A, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+size_t sweep_smem_bytes(const Problem& P, int wpb, int G) {
+  size_t b = (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4);
+  if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);
+  if (P.model == kEA) b += (size_t)2 * P.L * P.Wr1 * 4;
+  return b;
+}
+
+cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const SweepLaunch& A, cudaStream_t st) {
+  if (A.n_active <= 0) return cudaSuccess;
+  const size_t smem = sweep_smem_bytes(P, A.wpb, G);
+  switch (P.model) {
+    case kIsing: return launch_sweep_m<kIsing>(G, P, S, A, smem, st);
+    case kPotts: return launch_sweep_m<kPotts>(G, P, S, A, smem, st);
+    case kEA: return launch_sweep_m<kEA>(G, P, S, A, smem, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// One CTA per possible pair of either parity; CTAs of the other parity exit.
+cudaError_t launch_exchange(const Problem& P, const DevState& S, cudaStream_t st) {
+  const int pairs = P.h / 2;
+  if (pairs <= 0) return cudaSuccess;
+  const int threads = P.m < 128 ? ((P.m + 31) / 32) * 32 : 128;
+  k_exchange<<<pairs, threads, (size_t)P.m * sizeof(int), st>>>(P, S);
+  return cudaGetLastError();
+}
+
+__global__ void k_advance_clock(DevState S, uint32_t sweeps) {
+  S.clock[0] += sweeps;
+  S.clock[1] += 1;
+}
+
+cudaError_t launch_advance_clock(const DevState& S, uint32_t sweeps, cudaStream_t st) {
+  k_advance_clock<<<1, 1, 0, st>>>(S, sweeps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flat_merge(const Problem& P, const DevState& S, cudaStream_t st) {
+  k_flat_merge<<<P.h, 256, 0, st>>>(P, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Problem& P, const DevState& S, cudaStream_t st) {
+  k_init_lattice<<<(P.n_walkers + 63) / 64, 64, 0, st>>>(P, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_descent(const Problem& P, const DevState& S, uint64_t n_att, cudaStream_t st) {
+  k_descent<<<(P.n_walkers + 63) / 64, 64, 0, st>>>(P, S, n_att);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_entry(const Problem& P, const DevState& S, uint64_t budget, cudaStream_t st) {
+  k_entry<<<(P.n_walkers + 63) / 64, 64, 0, st>>>(P, S, budget);
+  return cudaGetLastError();
+}
+
+}  // namespace rewl

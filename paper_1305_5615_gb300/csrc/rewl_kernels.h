@@ -1,0 +1,22 @@
+// rewl_kernels.h -- launch wrappers of the device phases (rewl_kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "rewl_layout.h"
+
+namespace rewl {
+
+size_t sweep_smem_bytes(const Problem& P, int wpb, int G);
+cudaError_t prepare_sweep(int G, int model);
+cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const SweepLaunch& A, cudaStream_t st);
+cudaError_t launch_exchange(const Problem& P, const DevState& S, cudaStream_t st);
+cudaError_t launch_advance_clock(const DevState& S, uint32_t sweeps, cudaStream_t st);
+cudaError_t launch_flat_merge(const Problem& P, const DevState& S, cudaStream_t st);
+cudaError_t launch_init(const Problem& P, const DevState& S, cudaStream_t st);
+cudaError_t launch_descent(const Problem& P, const DevState& S, uint64_t n_att, cudaStream_t st);
+cudaError_t launch_entry(const Problem& P, const DevState& S, uint64_t budget, cudaStream_t st);
+
+}  // namespace rewl

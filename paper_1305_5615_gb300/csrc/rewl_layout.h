@@ -1,0 +1,62 @@
+// rewl_layout.h -- device data layout and kernel arguments of one REWL solve.
+//
+// HBM layout (all walker-major; walker W = a*m + k is walker k of window a):
+//   lat   u32 [n_walkers][lat_words]   packed configurations
+//   E     i32 [n_walkers]              current energies
+//   lng   f64 [n_walkers][w]           ln g over the window's w bins
+//   H     u32 [n_walkers][w]           visit histogram of the iteration
+//   J     u32 [2][L][Wr1]              +-J couplings, bit 1 = J -1 (planes: right, down)
+//   win_start i32 [h], lnf f64 [h], iter i32 [h], done i32 [h]
+//   counters u64: wl_accept / near_ties / exact_tests [n_walkers], x_tried / x_accepted [h]
+#pragma once
+#include <cstdint>
+
+namespace rewl {
+
+enum Model : int { kIsing = 0, kPotts = 1, kEA = 2 };
+// 4th Philox counter word: one stream per purpose.
+enum Tag : uint32_t { kTagFlip = 0, kTagEntry = 1, kTagPerm = 2, kTagXacc = 3, kTagInit = 4, kTagCoupling = 5 };
+
+struct Problem {
+  int model, q, L, N;
+  int Wr;          // words per lattice row (1-bit or 4-bit sites)
+  int Wr1;         // words per row of a coupling plane
+  int lat_words;   // L * Wr
+  int e_min, e_step, n_bins;
+  int h, m, w, n_walkers;
+  uint32_t magic_L;  // ceil(2^32 / L): y = mulhi(site, magic_L) for site < N
+  uint32_t seed_lo, seed_hi;
+  double flatness, lnf_final;
+};
+
+struct DevState {
+  uint32_t* lat;
+  uint32_t* J;
+  int32_t* E;
+  double* lng;
+  uint32_t* H;
+  int32_t* win_start;
+  double* lnf;
+  int32_t* iter;
+  int32_t* done;
+  int32_t* n_done;
+  uint64_t* wl_accept;
+  uint64_t* near_ties;
+  uint64_t* exact_tests;
+  uint64_t* x_tried;
+  uint64_t* x_accepted;
+  int32_t* active;       // walker ids the sweep kernel runs, in order
+  int32_t* status;       // per walker: 0 ok, else a rewl_status
+  uint64_t* entry_t;     // per walker counter of the entry stream
+  uint32_t* seed_config; // restart configuration for the entry walk
+  uint64_t* clock;       // [0] sweeps done by the solve, [1] exchange rounds done
+};
+
+struct SweepLaunch {
+  uint32_t n_att;     // trials per walker in this launch (sweeps * N); the first
+                      // trial's index is clock[0] * N, read on the device
+  int n_active;       // walkers in `active`
+  int wpb;            // walkers per CTA
+};
+
+}  // namespace rewl

@@ -1,0 +1,47 @@
+"""CPU checks of the boundary: the library builds for sm_103a, loads, and
+exports every entry point that include/rewl.h declares.  No compute call is
+made (there is no GPU here)."""
+import os
+import re
+
+import pytest
+
+from paper_1305_5615_gb300 import rewl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rewl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rewl_[a-z_]+)\s*\(", src)) - {"rewl_alloc_fn", "rewl_free_fn"})
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("rewl_create", "rewl_step", "rewl_get_lng", "rewl_destroy"):
+        assert n in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = rewl.load()
+    for n in declared_functions():
+        assert hasattr(lib, n), n
+    assert sorted(rewl.EXPORTED) == declared_functions()
+
+
+def test_status_strings_need_no_gpu():
+    assert rewl.rewl_status_str(0) == "ok"
+    assert "window" in rewl.rewl_status_str(5)
+    p = rewl.rewl_params_default()
+    assert (p.sweeps_per_exchange, p.sweeps_per_flat_check, p.lnf0) == (100, 1000, 1.0)
+
+
+def test_create_fails_cleanly_without_a_suitable_device():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(rewl.RewlError) as e:
+        rewl.REWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0)
+    assert e.value.status in (3, 9)
