@@ -92,6 +92,8 @@ typedef struct {
   void* alloc_user;
   int32_t profile;               /* 1 = time every sweep launch with CUDA events on the solve's stream
                                     (plain mode); read back through rewl_info */
+  int32_t sweep_variant;         /* sweep kernel form, identical results: 0 = two-deep chain (default),
+                                    1 = staged one-deep chain */
 } rewl_params;
 
 /* Fills *p with the defaults above. */

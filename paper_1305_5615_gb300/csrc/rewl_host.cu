@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/rewl.h"
+#include "rewl.h"
 #include "rewl_device.cuh"
 #include "rewl_kernels.h"
 #include "rewl_layout.h"
@@ -142,7 +142,7 @@ static void choose_config(rewl_ctx* c, int n_sm) {
   if (wpb == 0) {
     wpb = std::max(1, 256 / G);
     const size_t budget = 200 * 1024;
-    while (wpb > 1 && sweep_smem_bytes(P, wpb, G) > budget) --wpb;
+    while (wpb > 1 && sweep_smem_bytes(P, wpb, G, c->params.sweep_variant) > budget) --wpb;
     const int spread = (P.n_walkers + n_sm - 1) / n_sm;  // at least one CTA per SM when possible
     wpb = std::max(1, std::min(wpb, spread));
   }
@@ -268,6 +268,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   if (prm.walkers_per_block < 0 || (G && prm.walkers_per_block * G > 256))
     return fail(REWL_EINVAL, "walkers_per_block %d", prm.walkers_per_block);
   if (prm.mode != REWL_MODE_PLAIN && prm.mode != REWL_MODE_GRAPH) return fail(REWL_EINVAL, "mode %d", prm.mode);
+  if (prm.sweep_variant != 0 && prm.sweep_variant != 1) return fail(REWL_EINVAL, "sweep_variant %d", prm.sweep_variant);
   if (couplings)
     for (int i = 0; i < 2 * L * L; ++i)
       if (couplings[i] != 1 && couplings[i] != -1) return fail(REWL_EINVAL, "coupling %d is %d", i, couplings[i]);
@@ -417,9 +418,9 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   choose_config(c, n_sm);
   BAIL_CUDA(prepare_sweep(c->G, P.model));
-  if (sweep_smem_bytes(P, c->wpb, c->G) > 227 * 1024)
+  if (sweep_smem_bytes(P, c->wpb, c->G, prm.sweep_variant) > 227 * 1024)
     return bail(fail(REWL_EINVAL, "a walker needs %zu bytes of shared memory (window of %d bins)",
-                     sweep_smem_bytes(P, 1, c->G), P.w));
+                     sweep_smem_bytes(P, 1, c->G, prm.sweep_variant), P.w));
   st = upload_active(c);
   if (st != REWL_OK) return bail(st);
 #undef BAIL_CUDA
@@ -435,6 +436,7 @@ static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
   A.n_att = (uint32_t)(c->params.sweeps_per_exchange * c->P.N);
   A.n_active = c->n_active;
   A.wpb = c->wpb;
+  A.variant = c->params.sweep_variant;
   const bool timed = c->params.profile && c->params.mode == REWL_MODE_PLAIN;
   if (timed) {
     if ((int)c->ev_pool.size() < 2 * (c->ev_pending + 1)) {

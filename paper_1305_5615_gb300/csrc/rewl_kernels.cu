@@ -575,26 +575,34 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
           const bool inwin = (unsigned)bn < (unsigned)w;
           const int bl = inwin ? bn : bin;
           const int64_t fxn = s_fx[bl * wpb + lw];
+          const uint32_t hn = s_H[bl * wpb + lw];
           const int64_t d = (fx_cur - fxn) - cur.thr;
           bool acc = dbin == 0 || (inwin && d > kGuardFx);
-          if (dbin != 0 && inwin && d >= -kGuardFx && d <= kGuardFx) {
+          if (dbin != 0 && inwin && d >= -kGuardFx && d <= kGuardFx) {  // rare: exact FP64 test
             const uint64_t t = t0 + base + (uint32_t)j;
             const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-            acc = exact_accept(S, P, W, kexp, bin, h_cur, bn, s_H[bn * wpb + lw], u52_bits(r.z, r.w), n_tie);
+            acc = exact_accept(S, P, W, kexp, bin, h_cur, bn, hn, u52_bits(r.z, r.w), n_tie);
             ++n_exact;
           }
-          if (acc) {
-            accm |= 1u << j;
-            apply_move<MODEL>(s_lat, widx, wmask);
-            if (dbin != 0) {
-              s_fx[bin * wpb + lw] = fx_cur;
-              s_H[bin * wpb + lw] = h_cur;
-              bin = bn;
-              fx_cur = fxn;
-              h_cur = s_H[bn * wpb + lw];
-            }
-            ++n_acc;
+          // branch-free update: configuration word, write-back of the bin left, new state
+          const bool mv = acc && dbin != 0;
+          const uint32_t word = s_lat[widx];
+          uint32_t nword;
+          if constexpr (MODEL == kPotts) {
+            const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
+            nword = (word & ~(15u << sh)) | (nv << sh);
+          } else {
+            nword = word ^ wmask;
           }
+          s_lat[widx] = acc ? nword : word;
+          const int wb = (mv ? bin : bl) * wpb + lw;  // write-back target (a harmless rewrite of bl when no move)
+          s_fx[wb] = mv ? fx_cur : fxn;
+          s_H[wb] = mv ? h_cur : hn;
+          accm |= (uint32_t)acc << j;
+          n_acc += acc;
+          bin = mv ? bn : bin;
+          fx_cur = mv ? fxn : fx_cur;
+          h_cur = mv ? hn : h_cur;
           fx_cur += lnf_fx;  // ln g(E) += ln f on the shadow
           ++h_cur;           // H(E) += 1
         }
@@ -622,6 +630,245 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
       const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
       S.lng[g] = bits_to_double(add_pow2_repeated(double_to_bits(S.lng[g]), kx, c));
       S.H[g] = hs;
+    }
+  }
+  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
+    const int l = i / P.lat_words, j = i - l * P.lat_words;
+    S.lat[(size_t)S.active[first + l] * P.lat_words + j] = s_lat[j * wpb + l];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The WL sweep kernel, two-deep chain form.  Same trials, order and results
+// as k_sweep_spec; the sequential phase is reorganised around its critical
+// path.  While trial j resolves, lane 0 already loads the ln g shadow of both
+// bins trial j+1 can target (from the current bin, and from trial j's new
+// bin); once trial j's outcome is known one of the two is selected, with the
+// register value forwarded when the target is the bin trial j just left.
+// H is not kept during the launch: the shadow of a bin grows by exactly
+// ln f (in 2^-40 units) per visit, so the visit count of every bin is
+// (shadow_end - shadow_start) / ln f, and the write-back adds it to H and
+// applies the same number of FP64 additions to ln g.  The shadow array
+// carries kGuardBins unused bins on each side so that speculative loads
+// need no clamping.
+// ---------------------------------------------------------------------------
+constexpr int kGuardBins = 4;
+
+// exact FP64 re-evaluation from visit counts reconstructed from the shadow
+__device__ __noinline__ bool exact_accept_fx(const DevState& S, const Problem& P, int W, int k, int bin,
+                                             int64_t fx_cur, int bn, int64_t fx_new, uint64_t k52, uint64_t& n_tie) {
+  const double* lngW = S.lng + (size_t)W * P.w;
+  const int sh = kFxBits - k;
+  const uint64_t vc0 = double_to_bits(lngW[bin]), vn0 = double_to_bits(lngW[bn]);
+  const uint32_t cc = (uint32_t)((fx_cur - to_fx(vc0)) >> sh);
+  const uint32_t cn = (uint32_t)((fx_new - to_fx(vn0)) >> sh);
+  const double vc = bits_to_double(add_pow2_repeated(vc0, k, cc));
+  const double vn = bits_to_double(add_pow2_repeated(vn0, k, cn));
+  const double delta = __dsub_rn(vc, vn);
+  if (delta >= 0.0) return true;
+  const double u = __dmul_rn(__ull2double_rn(2ull * k52 + 1ull), 0x1p-53);
+  const double lu = log(u);
+  if (fabs(__dsub_rn(lu, delta)) < 1e-12) ++n_tie;
+  return lu < delta;
+}
+
+template <int MODEL>
+__device__ __forceinline__ void apply_move_if(uint32_t* s_lat, uint32_t widx, uint32_t wmask, bool acc) {
+  if constexpr (MODEL == kPotts) {
+    if (acc) {
+      const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
+      s_lat[widx] = (s_lat[widx] & ~(15u << sh)) | (nv << sh);
+    }
+  } else {
+    atomicXor(&s_lat[widx], acc ? wmask : 0u);
+  }
+}
+
+template <int MODEL, int G>
+__global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, SweepLaunch A) {
+  static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int wpb = A.wpb;
+  const int wpad = P.w + 2 * kGuardBins;
+  StagedTrial* s_stage = reinterpret_cast<StagedTrial*>(smem);                 // [wpb][G]
+  int64_t* s_fx = reinterpret_cast<int64_t*>(s_stage + (G > 1 ? (size_t)wpb * G : 0));  // [wpad][wpb]
+  uint32_t* s_lat = reinterpret_cast<uint32_t*>(s_fx + (size_t)wpad * wpb);
+  uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
+  const int nthr = blockDim.x;
+  const int tid = threadIdx.x;
+  const int first = blockIdx.x * wpb;
+  const int nloc = min(wpb, A.n_active - first);
+
+  for (int i = tid; i < nloc * wpad; i += nthr) {
+    const int l = i / wpad, bp = i - l * wpad, b = bp - kGuardBins;
+    int64_t v = 0;
+    if (b >= 0 && b < P.w) v = to_fx(double_to_bits(S.lng[(size_t)S.active[first + l] * P.w + b]));
+    s_fx[bp * wpb + l] = v;
+  }
+  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
+    const int l = i / P.lat_words, j = i - l * P.lat_words;
+    s_lat[j * wpb + l] = S.lat[(size_t)S.active[first + l] * P.lat_words + j];
+  }
+  if (MODEL == kEA)
+    for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
+  __syncthreads();
+
+  const int lw = tid / G, lane = tid % G;
+  bool valid = lw < nloc;
+  int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
+  if (valid) {
+    W = S.active[first + lw];
+    a = W / P.m;
+    wstart = S.win_start[a];
+    bin = (S.E[W] - P.e_min) / P.e_step - wstart;
+    if ((unsigned)bin >= (unsigned)P.w) {
+      if (lane == 0) S.status[W] = 6;
+      valid = false;
+    }
+  }
+  if (valid) {
+    kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
+    const int64_t lnf_fx = 1ll << (kFxBits - kexp);  // ln f >= 2^-39 (rewl_create checks ln f_final)
+    int64_t* fxp = s_fx + (size_t)kGuardBins * wpb + lw;  // fxp[b * wpb] = shadow of bin b, b in [-4, w+3]
+    int64_t fx_cur = fxp[bin * wpb];
+    uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
+    const uint32_t gm = group_mask<G>();
+    const int L = P.L, w = P.w;
+    const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
+    StagedTrial* my_stage = s_stage + (size_t)lw * G;
+
+    for (uint32_t base = 0; base < A.n_att; base += G) {
+      StagedTrial tr;
+      {
+        const uint64_t t = t0 + base + (uint32_t)lane;
+        const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+        const uint32_t site = scale32(r.x, (uint32_t)P.N);
+        const int y = (int)mulhi32(site, P.magic_L);
+        const int x = (int)site - y * L;
+        const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+        const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
+        tr.thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
+        const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
+        const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
+        uint32_t M = 0;
+        if constexpr (G > 1) {
+          const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
+          const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
+          const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
+          const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
+#pragma unroll
+          for (int i = 0; i < G - 1; ++i) {
+            const uint32_t pi = __shfl_sync(gm, pk, i, G);
+            const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
+            M |= (hit && i < lane) ? (1u << i) : 0u;
+          }
+        }
+        tr.pk = (uint32_t)(ev.dbin + 8) | (pv << 8) | (pk << 16);
+        tr.mask = M;
+        tr.widx = ev.widx;
+        tr.wmask = ev.wmask;
+        if constexpr (G > 1) my_stage[lane] = tr;
+      }
+      if constexpr (G > 1) __syncwarp(gm);
+
+      if (lane == 0) {
+        const int n_here = (int)min((uint32_t)G, A.n_att - base);
+        uint32_t accm = 0;
+        StagedTrial cc = tr, cn = tr;  // trial j and trial j+1
+        if constexpr (G > 1) {
+          cc = my_stage[0];
+          cn = my_stage[n_here > 1 ? 1 : 0];
+        }
+        int dj = (int)(cc.pk & 0xffu) - 8;
+        int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of trial 0's target bin
+#pragma unroll 1
+        for (int j = 0; j < n_here; ++j) {
+          // -- loads that do not depend on trial j's outcome go first: shared-memory
+          //    operations issue in order, so they must not queue behind its stores
+          StagedTrial cnn = cn;
+          if constexpr (G > 1) cnn = my_stage[min(j + 2, n_here - 1)];
+          const int dn = (int)(cn.pk & 0xffu) - 8;
+          int bn = bin + dj;
+          int64_t cand_stay = fxp[(bin + dn) * wpb];  // trial j+1's target if trial j stays
+          int64_t cand_move = fxp[(bn + dn) * wpb];   // trial j+1's target if trial j moves
+          uint32_t widx = cc.widx, wmask = cc.wmask;
+          uint32_t word = s_lat[widx];
+          // -- trial j, fast test: accept iff (shadow_old - shadow_new) - ln u > guard
+          bool inwin = (unsigned)bn < (unsigned)w;
+          const int64_t lim_acc = fx_cur - cc.thr - kGuardFx;   // accept iff fxn < lim_acc
+          const int64_t lim_rej = fx_cur - cc.thr + kGuardFx;   // reject iff fxn > lim_rej
+          bool acc = dj == 0 || (inwin && fxn < lim_acc);
+          const bool band = dj != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
+          const bool conflict = (accm & cc.mask) != 0u;
+          if (conflict || band) {  // rare: re-evaluate on the current configuration and/or test exactly
+            if (conflict) {
+              const TrialEval<MODEL> e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cc.pk >> 16) & 0xffu),
+                                                           (int)(cc.pk >> 24), (cc.pk >> 8) & 0xffu);
+              dj = e2.dbin;
+              widx = e2.widx;
+              wmask = e2.wmask;
+              word = s_lat[widx];
+              bn = bin + dj;
+              inwin = (unsigned)bn < (unsigned)w;
+              fxn = fxp[bn * wpb];
+              cand_move = fxp[(bn + dn) * wpb];
+            }
+            const int64_t dd = (fx_cur - fxn) - cc.thr;
+            acc = dj == 0 || (inwin && dd > kGuardFx);
+            if (dj != 0 && inwin && dd >= -kGuardFx && dd <= kGuardFx) {
+              const uint64_t t = t0 + base + (uint32_t)j;
+              const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+              acc = exact_accept_fx(S, P, W, kexp, bin, fx_cur, bn, fxn, u52_bits(r.z, r.w), n_tie);
+              ++n_exact;
+            }
+          }
+          const bool mv = acc && dj != 0;
+          // -- stores of trial j
+          uint32_t nword;
+          if constexpr (MODEL == kPotts) {
+            const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
+            nword = (word & ~(15u << sh)) | (nv << sh);
+          } else {
+            nword = word ^ wmask;
+          }
+          s_lat[widx] = acc ? nword : word;
+          if (mv) fxp[bin * wpb] = fx_cur;  // write back the shadow of the bin left
+          accm |= (uint32_t)acc << j;
+          // -- next state
+          const int64_t fwd = (dn == -dj) ? fx_cur : cand_move;  // trial j+1 targets the bin just left
+          fx_cur = (mv ? fxn : fx_cur) + lnf_fx;                // ln g(E) += ln f on the shadow
+          fxn = mv ? fwd : cand_stay;
+          bin = mv ? bn : bin;
+          cc = cn;
+          cn = cnn;
+          dj = dn;
+        }
+        n_acc += (uint64_t)__popc(accm);
+      }
+      if constexpr (G > 1) __syncwarp(gm);
+    }
+    if (lane == 0) {
+      fxp[bin * wpb] = fx_cur;
+      S.E[W] = P.e_min + (wstart + bin) * P.e_step;
+      S.wl_accept[W] += n_acc;
+      S.near_ties[W] += n_tie;
+      S.exact_tests[W] += n_exact;
+    }
+  }
+  __syncthreads();
+
+  // write back: visits = (shadow_end - shadow_start) / ln f; H += visits and the same number of
+  // FP64 additions of ln f to ln g
+  for (int i = tid; i < nloc * P.w; i += nthr) {
+    const int l = i / P.w, b = i - l * P.w;
+    const int Wl = S.active[first + l];
+    const size_t g = (size_t)Wl * P.w + b;
+    const uint64_t v0 = double_to_bits(S.lng[g]);
+    const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
+    const uint32_t c = (uint32_t)((s_fx[(b + kGuardBins) * wpb + l] - to_fx(v0)) >> (kFxBits - kx));
+    if (c) {
+      S.lng[g] = bits_to_double(add_pow2_repeated(v0, kx, c));
+      S.H[g] += c;
     }
   }
   for (int i = tid; i < nloc * P.lat_words; i += nthr) {
@@ -773,13 +1020,15 @@ __global__ void k_flat_merge(Problem P, DevState S) {
 // ---------------------------------------------------------------------------
 // G <= 4 lanes per walker: k_sweep; G >= 8: the speculative k_sweep_spec.
 template <int MODEL, int G>
-static auto sweep_kernel() {
-  return k_sweep_spec<MODEL, G>;
+static auto sweep_kernel(int variant) {
+  return variant == kSweepStaged ? k_sweep_spec<MODEL, G> : k_sweep_chain<MODEL, G>;
 }
 
 template <int MODEL, int G>
 static cudaError_t prepare_sweep_t() {
-  return cudaFuncSetAttribute(sweep_kernel<MODEL, G>(), cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_spec<MODEL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sweep_chain<MODEL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 template <int MODEL>
@@ -809,7 +1058,7 @@ template <int MODEL, int G>
 static cudaError_t launch_sweep_t(const Problem& P, const DevState& S, const SweepLaunch& A, size_t smem,
                                   cudaStream_t st) {
   const int blocks = (A.n_active + A.wpb - 1) / A.wpb;
-  sweep_kernel<MODEL, G>()<<<blocks, A.wpb * G, smem, st>>>(P, S, A);
+  sweep_kernel<MODEL, G>(A.variant)<<<blocks, A.wpb * G, smem, st>>>(P, S, A);
   return cudaGetLastError();
 }
 
@@ -827,8 +1076,9 @@ static cudaError_t launch_sweep_m(int G, const Problem& P, const DevState& S, co
   return cudaErrorInvalidValue;
 }
 
-size_t sweep_smem_bytes(const Problem& P, int wpb, int G) {
-  size_t b = (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4);
+size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
+  size_t b = variant == kSweepStaged ? (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4)
+                                     : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
   if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);
   if (P.model == kEA) b += (size_t)2 * P.L * P.Wr1 * 4;
   return b;
@@ -836,7 +1086,7 @@ size_t sweep_smem_bytes(const Problem& P, int wpb, int G) {
 
 cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const SweepLaunch& A, cudaStream_t st) {
   if (A.n_active <= 0) return cudaSuccess;
-  const size_t smem = sweep_smem_bytes(P, A.wpb, G);
+  const size_t smem = sweep_smem_bytes(P, A.wpb, G, A.variant);
   switch (P.model) {
     case kIsing: return launch_sweep_m<kIsing>(G, P, S, A, smem, st);
     case kPotts: return launch_sweep_m<kPotts>(G, P, S, A, smem, st);

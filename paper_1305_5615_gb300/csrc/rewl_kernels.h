@@ -9,7 +9,7 @@
 
 namespace rewl {
 
-size_t sweep_smem_bytes(const Problem& P, int wpb, int G);
+size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant);
 cudaError_t prepare_sweep(int G, int model);
 cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const SweepLaunch& A, cudaStream_t st);
 cudaError_t launch_exchange(const Problem& P, const DevState& S, cudaStream_t st);

@@ -52,11 +52,17 @@ struct DevState {
   uint64_t* clock;       // [0] sweeps done by the solve, [1] exchange rounds done
 };
 
+// Sweep kernel variants (identical results): the staged form keeps H in
+// shared memory and runs a one-deep sequential chain; the chain form
+// speculates two deep and rebuilds H from the shadow.
+enum SweepVariant : int { kSweepChain = 0, kSweepStaged = 1 };
+
 struct SweepLaunch {
   uint32_t n_att;     // trials per walker in this launch (sweeps * N); the first
                       // trial's index is clock[0] * N, read on the device
   int n_active;       // walkers in `active`
   int wpb;            // walkers per CTA
+  int variant;        // SweepVariant
 };
 
 }  // namespace rewl

@@ -49,7 +49,8 @@ class rewl_params(ctypes.Structure):
                 ("lnf0", ctypes.c_double), ("entry_max_sweeps", ctypes.c_int32), ("discovery_sweeps", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int64), ("stream", ctypes.c_void_p), ("lanes_per_walker", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("mode", ctypes.c_int32), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("profile", ctypes.c_int32)]
+                ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("profile", ctypes.c_int32),
+                ("sweep_variant", ctypes.c_int32)]
 
 
 class rewl_info(ctypes.Structure):
@@ -228,7 +229,8 @@ class REWL:
     def __init__(self, model, L, windows, overlap, walkers_per_window, flatness, lnf_final, seed, q=2,
                  couplings=None, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
                  entry_max_sweeps=1000, discovery_sweeps=200, timeout_ms=0, lanes_per_walker=0,
-                 walkers_per_block=0, mode=MODE_PLAIN, stream=None, torch_allocator=False, profile=False):
+                 walkers_per_block=0, mode=MODE_PLAIN, stream=None, torch_allocator=False, profile=False,
+                 sweep_variant=0):
         if isinstance(model, str):
             model = MODELS[model]
         p = rewl_params_default()
@@ -236,6 +238,7 @@ class REWL:
         p.entry_max_sweeps, p.discovery_sweeps, p.timeout_ms = entry_max_sweeps, discovery_sweeps, timeout_ms
         p.lanes_per_walker, p.walkers_per_block, p.mode = lanes_per_walker, walkers_per_block, mode
         p.profile = 1 if profile else 0
+        p.sweep_variant = sweep_variant
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._keep = None
