@@ -781,67 +781,90 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
         }
         int dj = (int)(cc.pk & 0xffu) - 8;
         int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of trial 0's target bin
+        int j = 0;
+        while (j < n_here) {
+          // ---- fast loop: no call and no large branch body inside; a trial that needs
+          //      re-evaluation (conflict) or the exact test (band) leaves the loop
 #pragma unroll 1
-        for (int j = 0; j < n_here; ++j) {
-          // -- loads that do not depend on trial j's outcome go first: shared-memory
-          //    operations issue in order, so they must not queue behind its stores
-          StagedTrial cnn = cn;
-          if constexpr (G > 1) cnn = my_stage[min(j + 2, n_here - 1)];
-          const int dn = (int)(cn.pk & 0xffu) - 8;
-          int bn = bin + dj;
-          int64_t cand_stay = fxp[(bin + dn) * wpb];  // trial j+1's target if trial j stays
-          int64_t cand_move = fxp[(bn + dn) * wpb];   // trial j+1's target if trial j moves
+          for (; j < n_here; ++j) {
+            // loads that do not depend on trial j's outcome first (shared-memory operations
+            // issue in order and must not queue behind trial j's stores)
+            StagedTrial cnn = cn;
+            if constexpr (G > 1) cnn = my_stage[min(j + 2, n_here - 1)];
+            const int dn = (int)(cn.pk & 0xffu) - 8;
+            const int bn = bin + dj;
+            const int64_t cand_stay = fxp[(bin + dn) * wpb];  // trial j+1's target if trial j stays
+            const int64_t cand_move = fxp[(bn + dn) * wpb];   // trial j+1's target if trial j moves
+            const uint32_t word = s_lat[cc.widx];
+            // accept iff (shadow_old - shadow_new) - ln u > guard; reject iff < -guard
+            const bool inwin = (unsigned)bn < (unsigned)w;
+            const int64_t lim_acc = fx_cur - cc.thr - kGuardFx;
+            const int64_t lim_rej = fx_cur - cc.thr + kGuardFx;
+            const bool acc = dj == 0 || (inwin && fxn < lim_acc);
+            const bool band = dj != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
+            if (band || (accm & cc.mask) != 0u) break;
+            const bool mv = acc && dj != 0;
+            uint32_t nword;
+            if constexpr (MODEL == kPotts) {
+              const uint32_t sh = cc.wmask & 0xffu, nv = cc.wmask >> 8;
+              nword = (word & ~(15u << sh)) | (nv << sh);
+            } else {
+              nword = word ^ cc.wmask;
+            }
+            s_lat[cc.widx] = acc ? nword : word;
+            if (mv) fxp[bin * wpb] = fx_cur;  // write back the shadow of the bin left
+            accm |= (uint32_t)acc << j;
+            const int64_t fwd = (dn == -dj) ? fx_cur : cand_move;  // trial j+1 targets the bin just left
+            fx_cur = (mv ? fxn : fx_cur) + lnf_fx;                // ln g(E) += ln f on the shadow
+            fxn = mv ? fwd : cand_stay;
+            bin = mv ? bn : bin;
+            cc = cn;
+            cn = cnn;
+            dj = dn;
+          }
+          if (j >= n_here) break;
+          // ---- slow path for trial j: re-evaluate on the current configuration when an
+          //      accepted earlier trial of the group touched its neighbourhood, and decide
+          //      exactly in FP64 when the fast test falls in the guard band
           uint32_t widx = cc.widx, wmask = cc.wmask;
-          uint32_t word = s_lat[widx];
-          // -- trial j, fast test: accept iff (shadow_old - shadow_new) - ln u > guard
-          bool inwin = (unsigned)bn < (unsigned)w;
-          const int64_t lim_acc = fx_cur - cc.thr - kGuardFx;   // accept iff fxn < lim_acc
-          const int64_t lim_rej = fx_cur - cc.thr + kGuardFx;   // reject iff fxn > lim_rej
-          bool acc = dj == 0 || (inwin && fxn < lim_acc);
-          const bool band = dj != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
-          const bool conflict = (accm & cc.mask) != 0u;
-          if (conflict || band) {  // rare: re-evaluate on the current configuration and/or test exactly
-            if (conflict) {
-              const TrialEval<MODEL> e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cc.pk >> 16) & 0xffu),
-                                                           (int)(cc.pk >> 24), (cc.pk >> 8) & 0xffu);
-              dj = e2.dbin;
-              widx = e2.widx;
-              wmask = e2.wmask;
-              word = s_lat[widx];
-              bn = bin + dj;
-              inwin = (unsigned)bn < (unsigned)w;
-              fxn = fxp[bn * wpb];
-              cand_move = fxp[(bn + dn) * wpb];
-            }
-            const int64_t dd = (fx_cur - fxn) - cc.thr;
-            acc = dj == 0 || (inwin && dd > kGuardFx);
-            if (dj != 0 && inwin && dd >= -kGuardFx && dd <= kGuardFx) {
-              const uint64_t t = t0 + base + (uint32_t)j;
-              const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-              acc = exact_accept_fx(S, P, W, kexp, bin, fx_cur, bn, fxn, u52_bits(r.z, r.w), n_tie);
-              ++n_exact;
-            }
+          if ((accm & cc.mask) != 0u) {
+            const TrialEval<MODEL> e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cc.pk >> 16) & 0xffu),
+                                                         (int)(cc.pk >> 24), (cc.pk >> 8) & 0xffu);
+            dj = e2.dbin;
+            widx = e2.widx;
+            wmask = e2.wmask;
+          }
+          const int bn = bin + dj;
+          const bool inwin = (unsigned)bn < (unsigned)w;
+          fxn = fxp[bn * wpb];
+          const int64_t dd = (fx_cur - fxn) - cc.thr;
+          bool acc = dj == 0 || (inwin && dd > kGuardFx);
+          if (dj != 0 && inwin && dd >= -kGuardFx && dd <= kGuardFx) {
+            const uint64_t t = t0 + base + (uint32_t)j;
+            const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+            acc = exact_accept_fx(S, P, W, kexp, bin, fx_cur, bn, fxn, u52_bits(r.z, r.w), n_tie);
+            ++n_exact;
           }
           const bool mv = acc && dj != 0;
-          // -- stores of trial j
-          uint32_t nword;
-          if constexpr (MODEL == kPotts) {
-            const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
-            nword = (word & ~(15u << sh)) | (nv << sh);
-          } else {
-            nword = word ^ wmask;
+          if (acc) {
+            if constexpr (MODEL == kPotts) {
+              const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
+              s_lat[widx] = (s_lat[widx] & ~(15u << sh)) | (nv << sh);
+            } else {
+              s_lat[widx] ^= wmask;
+            }
           }
-          s_lat[widx] = acc ? nword : word;
-          if (mv) fxp[bin * wpb] = fx_cur;  // write back the shadow of the bin left
+          if (mv) fxp[bin * wpb] = fx_cur;
           accm |= (uint32_t)acc << j;
-          // -- next state
-          const int64_t fwd = (dn == -dj) ? fx_cur : cand_move;  // trial j+1 targets the bin just left
-          fx_cur = (mv ? fxn : fx_cur) + lnf_fx;                // ln g(E) += ln f on the shadow
-          fxn = mv ? fwd : cand_stay;
+          fx_cur = (mv ? fxn : fx_cur) + lnf_fx;
           bin = mv ? bn : bin;
-          cc = cn;
-          cn = cnn;
-          dj = dn;
+          ++j;
+          if (j < n_here) {  // re-prime the fast loop: trial j+1 and j+2, and trial j's target shadow
+            cc = cn;
+            if constexpr (G > 1) cn = my_stage[min(j + 1, n_here - 1)];
+            dj = (int)(cc.pk & 0xffu) - 8;
+            fxn = fxp[(bin + dj) * wpb];
+          }
         }
         n_acc += (uint64_t)__popc(accm);
       }
