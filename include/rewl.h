@@ -237,6 +237,54 @@ rewl_status rewl_set_state(rewl_handle h, const rewl_state* st);
 /* Frees all device and host memory of the handle.  NULL-safe. */
 void rewl_destroy(rewl_handle h);
 
+/*
+ * rewl_sweep_noalloc -- WL sweeps of walkers whose state the CALLER holds in
+ * its own device memory, without any allocation by the library.  The paper
+ * has no counterpart: this entry point exists for callers that cannot let a
+ * library allocate device memory when they run a sweep (code inside an arena
+ * or pool it does not control, a runtime whose allocator must not be
+ * re-entered, a process that reserved all device memory up front).
+ *
+ * It runs the same sweep kernel as rewl_step, with the same trials and the
+ * same bit-exact results, for d->sweeps sweeps starting at sweep index
+ * d->first_sweep (trial t = first_sweep * N + i), and nothing else: no
+ * exchange, no flatness check.  All pointers are DEVICE pointers owned by the
+ * caller, in the layouts of rewl_state: lattice [walkers][lattice_words],
+ * E [walkers], lng and H [walkers][window_bins] (updated in place);
+ * win_start and lnf [windows] (read only; lnf a power of two >= 2^-39);
+ * coupling_bits (+-J only, else NULL): two bit planes [right|down][L][ceil(L/32)],
+ * bit set = J = -1.  stream: cudaStream_t or NULL (legacy stream); the call
+ * is asynchronous on it.
+ *
+ * Working memory (walker list, status flags, sweep clock, counters) comes from
+ * one fixed array of about 128 KB compiled into the library, room for
+ * REWL_NOALLOC_MAX_WALKERS walkers; every GPU that loads the library keeps it
+ * until the process exits.  Every call on a device uses the same array and
+ * overwrites what the previous call left there (it clears what must start at
+ * zero itself), so calls whose work overlaps on the GPU race: order them on
+ * one stream or synchronise between them.  The first call on each device
+ * looks up the array's device address; make that first call before any
+ * stream capture.
+ * Errors: REWL_EINVAL (NULL pointer, bad descriptor, more than
+ * REWL_NOALLOC_MAX_WALKERS walkers, window too wide for shared memory),
+ * REWL_ENODEV, REWL_ECUDA.
+ */
+#define REWL_NOALLOC_MAX_WALKERS 4096
+typedef struct {
+  int32_t model, q, L;                        /* as rewl_create (dim 2, periodic) */
+  int32_t windows, walkers_per_window;        /* walker W = a * walkers_per_window + k */
+  int32_t window_bins;                        /* w */
+  int32_t e_min, e_step;                      /* energy of global bin b = e_min + b * e_step */
+  uint64_t seed;                              /* Philox key of the solve */
+  uint64_t first_sweep;                       /* sweep index of the first sweep */
+  int32_t sweeps;                             /* sweeps to run (>= 0) */
+  int32_t lanes_per_walker;                   /* 1, 2, 4, 8, 16 or 32; 0 = 32 */
+} rewl_sweep_desc;
+
+rewl_status rewl_sweep_noalloc(const rewl_sweep_desc* d, uint32_t* lattice, int32_t* E, double* lng, uint32_t* H,
+                               const uint32_t* coupling_bits, const int32_t* win_start, const double* lnf,
+                               void* stream);
+
 /* Static description of a status code. */
 const char* rewl_status_str(rewl_status s);
 

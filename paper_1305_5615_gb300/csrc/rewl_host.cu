@@ -233,6 +233,13 @@ const char* rewl_status_str(rewl_status s) {
 
 const char* rewl_last_error(void) { return g_last_error.c_str(); }
 
+}  // extern "C"
+
+// Lets the other translation units of the library report through rewl_last_error.
+void rewl_set_last_error(const char* msg) { g_last_error = msg; }
+
+extern "C" {
+
 rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_lattice* lattice,
                         const int8_t* couplings, int32_t windows, double overlap, int32_t walkers_per_window,
                         double flatness, double lnf_final, uint64_t seed, const rewl_params* params) {

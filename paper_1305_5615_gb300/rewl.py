@@ -23,7 +23,7 @@ STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: 
 
 EXPORTED = ["rewl_params_default", "rewl_create", "rewl_step", "rewl_get_lng", "rewl_get_window_lng",
             "rewl_get_info", "rewl_get_state", "rewl_set_state", "rewl_destroy", "rewl_status_str",
-            "rewl_last_error"]
+            "rewl_last_error", "rewl_sweep_noalloc"]
 
 
 class RewlError(RuntimeError):
@@ -60,6 +60,13 @@ class rewl_info(ctypes.Structure):
                [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
                 ("d2h_bytes", ctypes.c_int64)]
+
+
+class rewl_sweep_desc(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("q", ctypes.c_int32), ("L", ctypes.c_int32), ("windows", ctypes.c_int32),
+                ("walkers_per_window", ctypes.c_int32), ("window_bins", ctypes.c_int32), ("e_min", ctypes.c_int32),
+                ("e_step", ctypes.c_int32), ("seed", ctypes.c_uint64), ("first_sweep", ctypes.c_uint64),
+                ("sweeps", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32)]
 
 
 class rewl_state(ctypes.Structure):
@@ -113,6 +120,8 @@ def load(build_if_missing=True):
     L.rewl_status_str.restype = ctypes.c_char_p
     L.rewl_last_error.argtypes = []
     L.rewl_last_error.restype = ctypes.c_char_p
+    L.rewl_sweep_noalloc.argtypes = [ctypes.POINTER(rewl_sweep_desc)] + [P] * 8
+    L.rewl_sweep_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -197,6 +206,13 @@ def rewl_set_state(h, state):
 
 def rewl_destroy(h):
     load().rewl_destroy(h)
+
+
+def rewl_sweep_noalloc(desc, lattice, E, lng, H, coupling_bits, win_start, lnf, stream=None):
+    """WL sweeps on caller-owned device buffers (integer device addresses, e.g.
+    torch tensor .data_ptr()); the library allocates nothing for this call."""
+    ptrs = [ctypes.c_void_p(p) if p else None for p in (lattice, E, lng, H, coupling_bits, win_start, lnf, stream)]
+    _check(load().rewl_sweep_noalloc(ctypes.byref(desc), *ptrs), "rewl_sweep_noalloc")
 
 
 def rewl_status_str(status):
