@@ -316,23 +316,116 @@ def run_gb300(args, wl, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+SERVED_MIX = (("ea", (12, 16, 20, 24, 32), 2), ("ising", (16, 24, 32), 2), ("potts", (16, 24, 32), 10))
+
+
+def served_requests(n, seed):
+    """The served stream: model uniform over {+-J, Ising, Potts q=10} (1/3 each),
+    L uniform over the model's sizes, 8 windows at 75% overlap x 4 walkers,
+    flatness 0.8, ln f -> 1e-6, request seed = request index (+-J couplings
+    drawn from it with p = 1/2)."""
+    import numpy as np
+
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        model, sizes, q = SERVED_MIX[int(rng.integers(3))]
+        out.append(dict(model=model, L=int(sizes[int(rng.integers(len(sizes)))]), q=q, seed=i))
+    return out
+
+
+def run_served(args, world, rank, local):
+    """Poisson stream of DOS requests through the request server (continuous
+    batching); p50/p99 latency from arrival to result and aggregate attempts/s.
+    The same requests are also solved one after another in plain form for the
+    comparison (--plain-requests of them)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    reqs = served_requests(args.requests, args.seed)
+    rng = np.random.default_rng(args.seed + 1)
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=len(reqs))) if args.rate > 0 else np.zeros(len(reqs))
+    S = rewl.RewlServer(device_bytes=args.server_gb << 30, max_running=args.slots)
+    ids, t_sub = [], []
+    t0 = time.perf_counter()
+    nxt = 0
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and arrivals[nxt] <= now:
+            r = reqs[nxt]
+            ids.append(S.submit(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"]))
+            t_sub.append(time.perf_counter() - t0)
+            nxt += 1
+        st = S.run(1)
+        if nxt == len(reqs) and st["running"] == 0 and st["queued"] == 0:
+            break
+        if st["running"] == 0 and st["queued"] == 0 and nxt < len(reqs):
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+    t_end = time.perf_counter() - t0
+    lat, att, failed = [], 0, 0
+    for k, rid in enumerate(ids):
+        inf = S.poll(rid)
+        if inf["state"] != rewl.REQ_DONE:
+            failed += 1
+            continue
+        lat.append(1e3 * (t_sub[k] - arrivals[k]) + inf["latency_ms"])   # arrival -> result
+        att += inf["attempts"]
+    lat = np.array(lat)
+    served = {"requests": len(reqs), "failed": failed, "wall_s": t_end, "attempts": att,
+              "attempts_per_s": att / t_end, "p50_latency_s": float(np.percentile(lat, 50)) / 1e3,
+              "p99_latency_s": float(np.percentile(lat, 99)) / 1e3, "rate_per_s": args.rate, "slots": args.slots}
+    plain = None
+    if args.plain_requests > 0:
+        t1 = time.perf_counter()
+        pa = 0
+        for r in reqs[:args.plain_requests]:
+            D = rewl.REWL(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"])
+            D.step(0)
+            pa += D.info["attempts"]
+            D.close()
+        pt = time.perf_counter() - t1
+        plain = {"requests": args.plain_requests, "wall_s": pt, "attempts_per_s": pa / pt,
+                 "mean_service_s": pt / args.plain_requests}
+    if rank == 0:
+        print(json.dumps({"metric": "served DOS requests: aggregate spin-flip attempts/s; p50/p99 arrival->result",
+                          "value": served["attempts_per_s"], "unit": "attempts/s", "n_gpus": world,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "served-stream", "desc": "Poisson stream; +-J L in {12..32}, Ising and "
+                                     "Potts q=10 L in {16,24,32}; 8 windows x 4 walkers; ln f -> 1e-6"},
+                          "served": served, "plain_one_at_a_time": plain}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["served-stream"])
     ap.add_argument("--mode", default="plain", choices=["plain", "graph"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--requests", type=int, default=96, help="served-stream: number of requests")
+    ap.add_argument("--rate", type=float, default=0.0, help="served-stream: Poisson arrivals per second (0 = all at once)")
+    ap.add_argument("--slots", type=int, default=1024, help="served-stream: request slots")
+    ap.add_argument("--server-gb", type=int, default=64, help="served-stream: device-memory budget in GiB")
+    ap.add_argument("--plain-requests", type=int, default=0, help="served-stream: also solve this many one by one")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    wl = WORKLOADS[args.workload]
     world, rank, local = dist_setup()
+    if args.workload == "served-stream":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the served stream has no CPU reference arm"}))
+            return
+        run_served(args, world, rank, local)
+        return
+    wl = WORKLOADS[args.workload]
     if world > 1 and args.impl == "gb300":
         import torch.distributed as dist
         import torch

@@ -238,6 +238,83 @@ rewl_status rewl_set_state(rewl_handle h, const rewl_state* st);
 void rewl_destroy(rewl_handle h);
 
 /*
+ * Served form.  The paper runs one solve at a time (one walker per CPU core,
+ * conclusion paragraph); here many independent REWL solves -- different
+ * models, lattice sizes, disorder realisations -- run together on one GPU.
+ * Each request is exactly the method of rewl_create / rewl_step (WL
+ * paragraph, Eq. (1), merge paragraph) with its own seed and schedule, so its
+ * result is bit-identical to the one it gets alone.
+ *
+ * Requests are queued at submission (inputs are copied) and admitted first
+ * come, first served while a slot (max_running) and the device-memory budget
+ * allow; the memory a request may need is estimated from its sizes with the
+ * widest window its energy range allows.  rewl_server_run advances the server
+ * by rounds: admission, then for every running request one block of
+ * sweeps_per_exchange sweeps, one exchange round and, when due, the flatness
+ * check -- one launch per model for the sweeps of all running walkers, one
+ * launch each for the exchanges, clocks and flatness checks of all requests.
+ * Finished requests are retired at the end of the round: their joined ln g is
+ * read back (rewl_server_result) and their memory returns to the budget.
+ * The server is internally synchronised: any thread may call it.
+ */
+typedef struct rewl_server* rewl_server_handle;
+
+typedef struct {
+  rewl_model model;
+  rewl_lattice lattice;
+  const int8_t* couplings;       /* +-J only, as rewl_create; copied at submission */
+  int32_t windows;
+  double overlap;
+  int32_t walkers_per_window;
+  double flatness;
+  double lnf_final;
+  uint64_t seed;
+} rewl_request;
+
+enum { REWL_REQ_QUEUED = 0, REWL_REQ_RUNNING = 1, REWL_REQ_DONE = 2, REWL_REQ_FAILED = 3, REWL_REQ_CANCELLED = 4 };
+
+typedef struct {
+  int32_t state;        /* REWL_REQ_* */
+  int32_t error;        /* rewl_status of a failed request */
+  double queued_ms;     /* submission -> admission (or end, if never admitted) */
+  double run_ms;        /* admission -> end */
+  double latency_ms;    /* submission -> end (so far, if not ended) */
+  int64_t sweeps;       /* sweeps run */
+  int64_t attempts;     /* WL trials of its walkers */
+  int64_t device_bytes; /* budget charged while running */
+} rewl_request_info;
+
+typedef struct {
+  int32_t running, queued, finished, failed;
+  int64_t rounds, attempts, device_bytes_in_use;
+} rewl_server_stats;
+
+/* device_bytes: memory budget for running requests; max_running: request slots;
+ * params: sweeps_per_exchange, sweeps_per_flat_check, lnf0, entry and
+ * discovery budgets, stream and allocator of every request (NULL = defaults).
+ * Errors: REWL_EINVAL, REWL_ENOMEM, REWL_ECUDA. */
+rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, int32_t max_running,
+                               const rewl_params* params);
+/* Queues a request; *id identifies it.  Errors: REWL_EINVAL (malformed),
+ * REWL_ENOMEM (larger than the whole budget).  Errors found at admission
+ * (e.g. REWL_EENTRY) end the request in REWL_REQ_FAILED. */
+rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* r, uint64_t* id);
+/* Runs up to max_rounds rounds (stops early when nothing runs or waits);
+ * *stats (may be NULL) describes the server afterwards.  Errors: REWL_ECUDA. */
+rewl_status rewl_server_run(rewl_server_handle s, int32_t max_rounds, rewl_server_stats* stats);
+/* State, timings and counters of a request.  Errors: REWL_ENOTFOUND. */
+rewl_status rewl_server_poll(rewl_server_handle s, uint64_t id, rewl_request_info* info);
+/* The joined, normalised ln g of a finished request (as rewl_get_lng).
+ * Errors: REWL_ENOTFOUND, REWL_EBUSY (not finished), REWL_EINVAL (capacity). */
+rewl_status rewl_server_result(rewl_server_handle s, uint64_t id, double* lng, int32_t capacity, int32_t* n_bins,
+                               int32_t* e_min, int32_t* e_step);
+/* Removes a queued request or stops a running one (its memory is freed at
+ * once; other requests are unaffected).  Errors: REWL_ENOTFOUND. */
+rewl_status rewl_server_cancel(rewl_server_handle s, uint64_t id);
+/* Frees everything the server holds.  NULL-safe. */
+void rewl_server_destroy(rewl_server_handle s);
+
+/*
  * rewl_sweep_noalloc -- WL sweeps of walkers whose state the CALLER holds in
  * its own device memory, without any allocation by the library.  The paper
  * has no counterpart: this entry point exists for callers that cannot let a

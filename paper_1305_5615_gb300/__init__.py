@@ -10,4 +10,4 @@ Python binding.
 """
 from .rewl import REWL, rewl_create, rewl_destroy, rewl_get_info, rewl_get_lng, rewl_get_state  # noqa: F401
 from .rewl import rewl_get_window_lng, rewl_params_default, rewl_set_state, rewl_step  # noqa: F401
-from .rewl import rewl_last_error, rewl_status_str, RewlError, unpack_lattice  # noqa: F401
+from .rewl import rewl_last_error, rewl_status_str, RewlError, unpack_lattice, RewlServer  # noqa: F401

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "rewl.h"
+#include "rewl_ctx.h"
 #include "rewl_device.cuh"
 #include "rewl_kernels.h"
 #include "rewl_layout.h"
@@ -41,35 +42,6 @@ rewl_status fail(rewl_status s, const char* fmt, ...) {
   } while (0)
 
 }  // namespace
-
-struct rewl_ctx {
-  Problem P{};
-  DevState S{};
-  rewl_params params{};
-  double overlap = 0.0;
-  int e_max = 0;
-  std::vector<int32_t> win_start;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::vector<void*> allocations;
-  int G = 32, wpb = 1;
-  int n_active = 0;
-  int n_done = 0;
-  uint64_t sweep_clock = 0, xround = 0;
-  uint64_t attempts = 0;        // WL trials of all walkers so far
-  int32_t* h_n_done = nullptr;  // pinned
-  cudaGraphExec_t graph = nullptr;
-  int graph_n_active = -1;
-  uint64_t h2d_bytes = 0, d2h_bytes = 0;
-  // sweep-launch timing (params.profile): event pairs pending since the last sync
-  std::vector<cudaEvent_t> ev_pool;
-  int ev_pending = 0;
-  int64_t sweep_launches = 0;
-  double sweep_ms = 0.0;
-
-  ~rewl_ctx();
-  void* dalloc(size_t bytes, rewl_status* st);
-};
 
 void* rewl_ctx::dalloc(size_t bytes, rewl_status* st) {
   void* p = nullptr;

@@ -207,183 +207,6 @@ __device__ __noinline__ bool exact_accept(const DevState& S, const Problem& P, i
   return lu < delta;
 }
 
-template <int MODEL, int G>
-__global__ void __launch_bounds__(256) k_sweep(Problem P, DevState S, SweepLaunch A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int wpb = A.wpb;
-  int64_t* s_fx = reinterpret_cast<int64_t*>(smem);
-  uint32_t* s_H = reinterpret_cast<uint32_t*>(s_fx + (size_t)P.w * wpb);
-  uint32_t* s_lat = s_H + (size_t)P.w * wpb;
-  uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
-  const int nthr = blockDim.x;
-  const int tid = threadIdx.x;
-  const int first = blockIdx.x * wpb;
-  const int nloc = min(wpb, A.n_active - first);
-
-  // ---- stage the walkers of this CTA into shared memory
-  for (int i = tid; i < nloc * P.w; i += nthr) {
-    const int l = i / P.w, b = i - l * P.w;
-    const size_t g = (size_t)S.active[first + l] * P.w + b;
-    s_fx[b * wpb + l] = to_fx(double_to_bits(S.lng[g]));
-    s_H[b * wpb + l] = S.H[g];
-  }
-  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
-    const int l = i / P.lat_words, j = i - l * P.lat_words;
-    s_lat[j * wpb + l] = S.lat[(size_t)S.active[first + l] * P.lat_words + j];
-  }
-  if (MODEL == kEA)
-    for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
-  __syncthreads();
-
-  const int lw = tid / G, lane = tid % G;
-  bool valid = lw < nloc;
-  int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
-  if (valid) {
-    W = S.active[first + lw];
-    a = W / P.m;
-    wstart = S.win_start[a];
-    bin = (S.E[W] - P.e_min) / P.e_step - wstart;
-    if ((unsigned)bin >= (unsigned)P.w) {  // cannot happen for a consistent state; never index with it
-      if (lane == 0) S.status[W] = 6;
-      valid = false;
-    }
-  }
-  if (valid) {
-    kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);  // ln f = 2^-kexp
-    const int64_t lnf_fx = kexp <= kFxBits ? (1ll << (kFxBits - kexp)) : 0;
-    int64_t fx_cur = s_fx[bin * wpb + lw];
-    uint32_t h_cur = s_H[bin * wpb + lw];
-    uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
-    const uint32_t gm = group_mask<G>();
-    const int L = P.L, Wr = P.Wr, w = P.w;
-    const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
-
-    for (uint32_t base = 0; base < A.n_att; base += G) {
-      // -- parallel part: lane draws trial base + lane
-      const uint64_t t = t0 + base + (uint32_t)lane;
-      const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-      const uint32_t site = scale32(r.x, (uint32_t)P.N);
-      const uint32_t yy = mulhi32(site, P.magic_L);
-      const uint32_t xx = site - yy * (uint32_t)L;
-      const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
-      const uint64_t k52 = u52_bits(r.z, r.w);
-      const float uf = __ull2float_rn(2ull * k52 + 1ull) * 0x1p-53f;
-      const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);  // ln u in units of 2^-40
-      const uint32_t packed = xx | (yy << 8) | (pv << 16);
-
-      // -- sequential part: the G trials in order (fewer in the last group
-      //    when the launch's trial count is not a multiple of G)
-      const int n_here = (int)min((uint32_t)G, A.n_att - base);
-#pragma unroll 1
-      for (int j = 0; j < n_here; ++j) {
-        const uint32_t pk = gshfl<G>(gm, packed, j);
-        const int64_t th = gshfl<G>(gm, thr, j);
-        gsync<G>(gm);  // previous trial's stores are visible to the whole group
-        const int x = pk & 0xff, y = (pk >> 8) & 0xff;
-        const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
-        const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
-        int dbin;
-        uint32_t word_idx, new_word;
-        if constexpr (MODEL == kPotts) {
-          const uint32_t v = potts_val(s_lat, wpb, lw, Wr, x, y);
-          uint32_t nv = v + 1u + (pk >> 16);
-          if (nv >= (uint32_t)P.q) nv -= (uint32_t)P.q;
-          const uint32_t n1 = potts_val(s_lat, wpb, lw, Wr, xr, y), n2 = potts_val(s_lat, wpb, lw, Wr, xl, y);
-          const uint32_t n3 = potts_val(s_lat, wpb, lw, Wr, x, yd), n4 = potts_val(s_lat, wpb, lw, Wr, x, yu);
-          dbin = (int)(n1 == v) + (int)(n2 == v) + (int)(n3 == v) + (int)(n4 == v) - (int)(n1 == nv) -
-                 (int)(n2 == nv) - (int)(n3 == nv) - (int)(n4 == nv);
-          word_idx = (uint32_t)((y * Wr + (x >> 3)) * wpb + lw);
-          const int sh = (x & 7) * 4;
-          new_word = (s_lat[word_idx] & ~(15u << sh)) | (nv << sh);
-        } else {
-          const uint32_t c = spin_bit(s_lat, wpb, lw, Wr, x, y);
-          const uint32_t nr = spin_bit(s_lat, wpb, lw, Wr, xr, y), nl = spin_bit(s_lat, wpb, lw, Wr, xl, y);
-          const uint32_t nd = spin_bit(s_lat, wpb, lw, Wr, x, yd), nu = spin_bit(s_lat, wpb, lw, Wr, x, yu);
-          uint32_t jr = 0, jl = 0, jd = 0, ju = 0;
-          if constexpr (MODEL == kEA) {
-            jr = coupling_bit(s_J, P.Wr1, 0, L, x, y);
-            jl = coupling_bit(s_J, P.Wr1, 0, L, xl, y);
-            jd = coupling_bit(s_J, P.Wr1, 1, L, x, y);
-            ju = coupling_bit(s_J, P.Wr1, 1, L, x, yu);
-          }
-          // bond satisfied iff J s s' = +1 iff (b ^ b' ^ jneg) == 0; dE = 4 * satisfied - 8
-          const int sat = (int)(((c ^ nr ^ jr) & 1u) == 0) + (int)(((c ^ nl ^ jl) & 1u) == 0) +
-                          (int)(((c ^ nd ^ jd) & 1u) == 0) + (int)(((c ^ nu ^ ju) & 1u) == 0);
-          dbin = sat - 2;
-          word_idx = (uint32_t)((y * Wr + (x >> 5)) * wpb + lw);
-          new_word = s_lat[word_idx] ^ (1u << (x & 31));
-        }
-        const int bn = bin + dbin;
-        bool acc;
-        int64_t fxn = fx_cur;
-        uint32_t hn = h_cur;
-        if (dbin == 0) {
-          acc = true;  // ln g(E_old) - ln g(E_new) = 0
-        } else if ((unsigned)bn >= (unsigned)w) {
-          acc = false;  // the move leaves the window
-        } else {
-          fxn = s_fx[bn * wpb + lw];
-          hn = s_H[bn * wpb + lw];
-          const int64_t d = (fx_cur - fxn) - th;
-          if (d > kGuardFx) {
-            acc = true;
-          } else if (d < -kGuardFx) {
-            acc = false;
-          } else {
-            const uint32_t r2 = gshfl<G>(gm, r.z, j), r3 = gshfl<G>(gm, r.w, j);
-            acc = exact_accept(S, P, W, kexp, bin, h_cur, bn, hn, u52_bits(r2, r3), n_tie);
-            ++n_exact;
-          }
-        }
-        gsync<G>(gm);  // all reads of this trial precede its stores
-        if (acc) {
-          if (lane == 0) s_lat[word_idx] = new_word;
-          if (dbin != 0) {
-            if (lane == 0) {
-              s_fx[bin * wpb + lw] = fx_cur;
-              s_H[bin * wpb + lw] = h_cur;
-            }
-            bin = bn;
-            fx_cur = fxn;
-            h_cur = hn;
-          }
-          ++n_acc;
-        }
-        fx_cur += lnf_fx;  // ln g(E) += ln f on the shadow
-        ++h_cur;           // H(E) += 1
-      }
-    }
-    gsync<G>(gm);
-    if (lane == 0) {
-      s_fx[bin * wpb + lw] = fx_cur;
-      s_H[bin * wpb + lw] = h_cur;
-      S.E[W] = P.e_min + (wstart + bin) * P.e_step;
-      S.wl_accept[W] += n_acc;
-      S.near_ties[W] += n_tie;
-      S.exact_tests[W] += n_exact;
-    }
-  }
-  __syncthreads();
-
-  // ---- write back: exact FP64 ln g from the visit counts of this launch
-  for (int i = tid; i < nloc * P.w; i += nthr) {
-    const int l = i / P.w, b = i - l * P.w;
-    const int Wl = S.active[first + l];
-    const size_t g = (size_t)Wl * P.w + b;
-    const uint32_t hs = s_H[b * wpb + l];
-    const uint32_t c = hs - S.H[g];
-    if (c) {
-      const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
-      S.lng[g] = bits_to_double(add_pow2_repeated(double_to_bits(S.lng[g]), kx, c));
-      S.H[g] = hs;
-    }
-  }
-  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
-    const int l = i / P.lat_words, j = i - l * P.lat_words;
-    S.lat[(size_t)S.active[first + l] * P.lat_words + j] = s_lat[j * wpb + l];
-  }
-}
-
 // ---------------------------------------------------------------------------
 // The WL sweep kernel, speculative form (G = 8, 16 or 32 lanes per walker).
 //
@@ -684,11 +507,12 @@ __device__ __forceinline__ void apply_move_if(uint32_t* s_lat, uint32_t widx, ui
   }
 }
 
+// Runs the sweeps of the nloc walkers wids[0..nloc) of one CTA (wpb walkers per CTA).
 template <int MODEL, int G>
-__global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, SweepLaunch A) {
+__device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevState& S, uint32_t n_att, int wpb,
+                                                 const int32_t* wids, int nloc) {
   static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
   extern __shared__ __align__(16) unsigned char smem[];
-  const int wpb = A.wpb;
   const int wpad = P.w + 2 * kGuardBins;
   StagedTrial* s_stage = reinterpret_cast<StagedTrial*>(smem);                 // [wpb][G]
   int64_t* s_fx = reinterpret_cast<int64_t*>(s_stage + (G > 1 ? (size_t)wpb * G : 0));  // [wpad][wpb]
@@ -696,18 +520,16 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
   uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
   const int nthr = blockDim.x;
   const int tid = threadIdx.x;
-  const int first = blockIdx.x * wpb;
-  const int nloc = min(wpb, A.n_active - first);
 
   for (int i = tid; i < nloc * wpad; i += nthr) {
     const int l = i / wpad, bp = i - l * wpad, b = bp - kGuardBins;
     int64_t v = 0;
-    if (b >= 0 && b < P.w) v = to_fx(double_to_bits(S.lng[(size_t)S.active[first + l] * P.w + b]));
+    if (b >= 0 && b < P.w) v = to_fx(double_to_bits(S.lng[(size_t)wids[l] * P.w + b]));
     s_fx[bp * wpb + l] = v;
   }
   for (int i = tid; i < nloc * P.lat_words; i += nthr) {
     const int l = i / P.lat_words, j = i - l * P.lat_words;
-    s_lat[j * wpb + l] = S.lat[(size_t)S.active[first + l] * P.lat_words + j];
+    s_lat[j * wpb + l] = S.lat[(size_t)wids[l] * P.lat_words + j];
   }
   if (MODEL == kEA)
     for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
@@ -717,7 +539,7 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
   bool valid = lw < nloc;
   int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
   if (valid) {
-    W = S.active[first + lw];
+    W = wids[lw];
     a = W / P.m;
     wstart = S.win_start[a];
     bin = (S.E[W] - P.e_min) / P.e_step - wstart;
@@ -737,7 +559,7 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
     StagedTrial* my_stage = s_stage + (size_t)lw * G;
 
-    for (uint32_t base = 0; base < A.n_att; base += G) {
+    for (uint32_t base = 0; base < n_att; base += G) {
       StagedTrial tr;
       {
         const uint64_t t = t0 + base + (uint32_t)lane;
@@ -772,7 +594,7 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
       if constexpr (G > 1) __syncwarp(gm);
 
       if (lane == 0) {
-        const int n_here = (int)min((uint32_t)G, A.n_att - base);
+        const int n_here = (int)min((uint32_t)G, n_att - base);
         uint32_t accm = 0;
         StagedTrial cc = tr, cn = tr;  // trial j and trial j+1
         if constexpr (G > 1) {
@@ -884,7 +706,7 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
   // FP64 additions of ln f to ln g
   for (int i = tid; i < nloc * P.w; i += nthr) {
     const int l = i / P.w, b = i - l * P.w;
-    const int Wl = S.active[first + l];
+    const int Wl = wids[l];
     const size_t g = (size_t)Wl * P.w + b;
     const uint64_t v0 = double_to_bits(S.lng[g]);
     const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
@@ -896,8 +718,14 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
   }
   for (int i = tid; i < nloc * P.lat_words; i += nthr) {
     const int l = i / P.lat_words, j = i - l * P.lat_words;
-    S.lat[(size_t)S.active[first + l] * P.lat_words + j] = s_lat[j * wpb + l];
+    S.lat[(size_t)wids[l] * P.lat_words + j] = s_lat[j * wpb + l];
   }
+}
+
+template <int MODEL, int G>
+__global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, SweepLaunch A) {
+  const int first = blockIdx.x * A.wpb;
+  sweep_chain_body<MODEL, G>(P, S, A.n_att, A.wpb, S.active + first, min(A.wpb, A.n_active - first));
 }
 
 // ---------------------------------------------------------------------------
@@ -905,10 +733,10 @@ __global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, Swee
 // (mod 2); walker k of window a is paired with walker sigma(k) of window a+1,
 // sigma a Fisher-Yates permutation from the round's own stream.
 // ---------------------------------------------------------------------------
-__global__ void k_exchange(Problem P, DevState S) {
+__device__ __forceinline__ void exchange_body(const Problem& P, const DevState& S, int pair_block) {
   extern __shared__ int sigma[];
   const uint32_t round = (uint32_t)S.clock[1];
-  const int a = 2 * (int)blockIdx.x + (int)(round & 1u);
+  const int a = 2 * pair_block + (int)(round & 1u);
   if (a + 1 >= P.h) return;
   if (S.done[a] || S.done[a + 1]) return;
   const int m = P.m;
@@ -962,11 +790,12 @@ __global__ void k_exchange(Problem P, DevState S) {
   if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&S.x_tried[a]), (unsigned long long)m);
 }
 
+__global__ void k_exchange(Problem P, DevState S) { exchange_body(P, S, (int)blockIdx.x); }
+
 // ---------------------------------------------------------------------------
 // Flatness, merge and f update.  One CTA per window.
 // ---------------------------------------------------------------------------
-__global__ void k_flat_merge(Problem P, DevState S) {
-  const int a = blockIdx.x;
+__device__ __forceinline__ void flat_merge_body(const Problem& P, const DevState& S, int a) {
   if (S.done[a]) return;
   __shared__ uint32_t r_min[32];
   __shared__ unsigned long long r_sum[32];
@@ -1036,6 +865,95 @@ __global__ void k_flat_merge(Problem P, DevState S) {
       atomicAdd(S.n_done, 1);
     }
   }
+}
+
+__global__ void k_flat_merge(Problem P, DevState S) { flat_merge_body(P, S, (int)blockIdx.x); }
+
+// ---------------------------------------------------------------------------
+// Served form: the same phase bodies over many request slots in one launch.
+// Sweep: one CTA per (slot, walker) of the model's walker list, G = 32.
+// Exchange: one CTA per (slot, window pair).  Clock: one thread per slot.
+// Flatness: one CTA per (slot, window), acting only on slots whose sweep
+// clock is at a multiple of their flatness period.  Every request keeps its
+// own schedule, streams and state, so its trajectory is the one it has alone.
+// ---------------------------------------------------------------------------
+template <int MODEL>
+__global__ void __launch_bounds__(32) k_sweep_batch(const BatchSlot* __restrict__ slots,
+                                                    const BatchWalker* __restrict__ list) {
+  __shared__ int32_t wid;
+  const BatchWalker bw = list[blockIdx.x];
+  const Problem P = slots[bw.slot].P;
+  const DevState S = slots[bw.slot].S;
+  const uint32_t n_att = slots[bw.slot].n_att;
+  if (!slots[bw.slot].active || S.done[bw.W / P.m]) return;  // uniform over the CTA
+  if (threadIdx.x == 0) wid = bw.W;
+  __syncthreads();
+  sweep_chain_body<MODEL, 32>(P, S, n_att, 1, &wid, 1);
+}
+
+__global__ void k_exchange_batch(const BatchSlot* __restrict__ slots, int max_pairs) {
+  const int s = (int)blockIdx.x / max_pairs, p = (int)blockIdx.x % max_pairs;
+  if (!slots[s].active) return;
+  const Problem P = slots[s].P;
+  const DevState S = slots[s].S;
+  exchange_body(P, S, p);
+}
+
+__global__ void k_advance_batch(const BatchSlot* __restrict__ slots, int n_slots) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots || !slots[s].active) return;
+  slots[s].S.clock[0] += slots[s].spe;
+  slots[s].S.clock[1] += 1;
+}
+
+__global__ void k_flat_batch(const BatchSlot* __restrict__ slots, int max_h) {
+  const int s = (int)blockIdx.x / max_h, a = (int)blockIdx.x % max_h;
+  if (!slots[s].active || a >= slots[s].P.h) return;
+  if (slots[s].S.clock[0] % slots[s].spf != 0) return;
+  const Problem P = slots[s].P;
+  const DevState S = slots[s].S;
+  flat_merge_body(P, S, a);
+}
+
+// Copies every slot's count of finished windows into one array (-1 for a free slot).
+__global__ void k_gather_done(const BatchSlot* __restrict__ slots, int n_slots, int32_t* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  out[s] = slots[s].active ? *slots[s].S.n_done : -1;
+}
+
+// k_sweep_batch has a few bytes of static shared memory, so its dynamic
+// allowance stays below the 227 KB per-CTA limit.
+constexpr int kBatchDynSmem = 226 * 1024;
+
+cudaError_t prepare_sweep_batch() {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<kIsing>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_sweep_batch<kPotts>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sweep_batch<kEA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+}
+
+cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, BatchWalker* const d_lists[3],
+                               const int n_list[3], const size_t smem[3], int max_pairs, int max_m, int max_h,
+                               cudaStream_t st) {
+  if (n_list[kIsing] > 0) k_sweep_batch<kIsing><<<n_list[kIsing], 32, smem[kIsing], st>>>(d_slots, d_lists[kIsing]);
+  if (n_list[kPotts] > 0) k_sweep_batch<kPotts><<<n_list[kPotts], 32, smem[kPotts], st>>>(d_slots, d_lists[kPotts]);
+  if (n_list[kEA] > 0) k_sweep_batch<kEA><<<n_list[kEA], 32, smem[kEA], st>>>(d_slots, d_lists[kEA]);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (max_pairs > 0) {
+    const int threads = max_m < 128 ? ((max_m + 31) / 32) * 32 : 128;
+    k_exchange_batch<<<n_slots * max_pairs, threads, (size_t)max_m * sizeof(int), st>>>(d_slots, max_pairs);
+  }
+  k_advance_batch<<<(n_slots + 127) / 128, 128, 0, st>>>(d_slots, n_slots);
+  k_flat_batch<<<n_slots * max_h, 256, 0, st>>>(d_slots, max_h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_done(const BatchSlot* d_slots, int n_slots, int32_t* out, cudaStream_t st) {
+  k_gather_done<<<(n_slots + 127) / 128, 128, 0, st>>>(d_slots, n_slots, out);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

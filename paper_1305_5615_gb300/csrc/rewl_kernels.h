@@ -19,4 +19,11 @@ cudaError_t launch_init(const Problem& P, const DevState& S, cudaStream_t st);
 cudaError_t launch_descent(const Problem& P, const DevState& S, uint64_t n_att, cudaStream_t st);
 cudaError_t launch_entry(const Problem& P, const DevState& S, uint64_t budget, cudaStream_t st);
 
+// served form (rewl_server.cu)
+cudaError_t prepare_sweep_batch();
+cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, BatchWalker* const d_lists[3],
+                               const int n_list[3], const size_t smem[3], int max_pairs, int max_m, int max_h,
+                               cudaStream_t st);
+cudaError_t launch_gather_done(const BatchSlot* d_slots, int n_slots, int32_t* out, cudaStream_t st);
+
 }  // namespace rewl

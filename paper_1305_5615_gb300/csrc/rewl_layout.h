@@ -65,4 +65,19 @@ struct SweepLaunch {
   int variant;        // SweepVariant
 };
 
+// One request slot of the served form: the request's sizes and device
+// arrays, as used by its own single-solve kernels.
+struct BatchSlot {
+  Problem P;
+  DevState S;
+  uint32_t n_att;   // trials per walker per block: sweeps_per_exchange * N
+  uint32_t spe;     // sweeps_per_exchange
+  uint32_t spf;     // sweeps_per_flat_check
+  int active;       // 0 = free slot
+};
+struct BatchWalker {
+  int slot;
+  int W;
+};
+
 }  // namespace rewl

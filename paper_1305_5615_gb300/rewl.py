@@ -23,7 +23,9 @@ STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: 
 
 EXPORTED = ["rewl_params_default", "rewl_create", "rewl_step", "rewl_get_lng", "rewl_get_window_lng",
             "rewl_get_info", "rewl_get_state", "rewl_set_state", "rewl_destroy", "rewl_status_str",
-            "rewl_last_error", "rewl_sweep_noalloc"]
+            "rewl_last_error", "rewl_sweep_noalloc", "rewl_server_create", "rewl_server_submit", "rewl_server_run",
+            "rewl_server_poll", "rewl_server_result", "rewl_server_cancel", "rewl_server_destroy"]
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 
 class RewlError(RuntimeError):
@@ -67,6 +69,24 @@ class rewl_sweep_desc(ctypes.Structure):
                 ("walkers_per_window", ctypes.c_int32), ("window_bins", ctypes.c_int32), ("e_min", ctypes.c_int32),
                 ("e_step", ctypes.c_int32), ("seed", ctypes.c_uint64), ("first_sweep", ctypes.c_uint64),
                 ("sweeps", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32)]
+
+
+class rewl_request(ctypes.Structure):
+    _fields_ = [("model", rewl_model), ("lattice", rewl_lattice), ("couplings", ctypes.c_void_p),
+                ("windows", ctypes.c_int32), ("overlap", ctypes.c_double), ("walkers_per_window", ctypes.c_int32),
+                ("flatness", ctypes.c_double), ("lnf_final", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class rewl_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("queued_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("sweeps", ctypes.c_int64),
+                ("attempts", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+class rewl_server_stats(ctypes.Structure):
+    _fields_ = [("running", ctypes.c_int32), ("queued", ctypes.c_int32), ("finished", ctypes.c_int32),
+                ("failed", ctypes.c_int32), ("rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
+                ("device_bytes_in_use", ctypes.c_int64)]
 
 
 class rewl_state(ctypes.Structure):
@@ -122,6 +142,21 @@ def load(build_if_missing=True):
     L.rewl_last_error.restype = ctypes.c_char_p
     L.rewl_sweep_noalloc.argtypes = [ctypes.POINTER(rewl_sweep_desc)] + [P] * 8
     L.rewl_sweep_noalloc.restype = ctypes.c_int
+    L.rewl_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(rewl_params)]
+    L.rewl_server_create.restype = ctypes.c_int
+    L.rewl_server_submit.argtypes = [P, ctypes.POINTER(rewl_request), ctypes.POINTER(ctypes.c_uint64)]
+    L.rewl_server_submit.restype = ctypes.c_int
+    L.rewl_server_run.argtypes = [P, ctypes.c_int32, ctypes.POINTER(rewl_server_stats)]
+    L.rewl_server_run.restype = ctypes.c_int
+    L.rewl_server_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(rewl_request_info)]
+    L.rewl_server_poll.restype = ctypes.c_int
+    L.rewl_server_result.argtypes = [P, ctypes.c_uint64, P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+    L.rewl_server_result.restype = ctypes.c_int
+    L.rewl_server_cancel.argtypes = [P, ctypes.c_uint64]
+    L.rewl_server_cancel.restype = ctypes.c_int
+    L.rewl_server_destroy.argtypes = [P]
+    L.rewl_server_destroy.restype = None
     _lib = L
     return L
 
@@ -295,6 +330,67 @@ class REWL:
     def set_state(self, state):
         rewl_set_state(self._h, state)
         self.info = rewl_get_info(self._h)
+
+
+class RewlServer:
+    """Served form: many REWL requests admitted by slots and device memory and
+    run together (rewl_server_* of include/rewl.h)."""
+
+    def __init__(self, device_bytes, max_running, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
+                 entry_max_sweeps=1000, discovery_sweeps=200, stream=None):
+        L = load()
+        p = rewl_params_default()
+        p.sweeps_per_exchange, p.sweeps_per_flat_check, p.lnf0 = sweeps_per_exchange, sweeps_per_flat_check, lnf0
+        p.entry_max_sweeps, p.discovery_sweeps = entry_max_sweeps, discovery_sweeps
+        if stream is not None:
+            p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
+        self._h = None
+        h = ctypes.c_void_p()
+        _check(L.rewl_server_create(ctypes.byref(h), int(device_bytes), int(max_running), ctypes.byref(p)),
+               "rewl_server_create")
+        self._h = h
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            load().rewl_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, model, L, windows, overlap, walkers_per_window, flatness, lnf_final, seed, q=2, couplings=None):
+        if isinstance(model, str):
+            model = MODELS[model]
+        cpl = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
+        r = rewl_request(rewl_model(model, q), rewl_lattice(2, L, L, 1), _p(cpl), windows, overlap,
+                         walkers_per_window, flatness, lnf_final, seed)
+        rid = ctypes.c_uint64()
+        _check(load().rewl_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "rewl_server_submit")
+        return rid.value
+
+    def run(self, max_rounds):
+        st = rewl_server_stats()
+        _check(load().rewl_server_run(self._h, int(max_rounds), ctypes.byref(st)), "rewl_server_run")
+        return {k: getattr(st, k) for k, _ in rewl_server_stats._fields_}
+
+    def poll(self, rid):
+        i = rewl_request_info()
+        _check(load().rewl_server_poll(self._h, rid, ctypes.byref(i)), "rewl_server_poll")
+        return {k: getattr(i, k) for k, _ in rewl_request_info._fields_}
+
+    def result(self, rid, capacity=1 << 16):
+        out = np.empty(capacity, np.float64)
+        n, e0, de = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(load().rewl_server_result(self._h, rid, _p(out), capacity, ctypes.byref(n), ctypes.byref(e0),
+                                         ctypes.byref(de)), "rewl_server_result")
+        return out[:n.value], e0.value, de.value
+
+    def cancel(self, rid):
+        _check(load().rewl_server_cancel(self._h, rid), "rewl_server_cancel")
 
 
 def unpack_lattice(words, L, model):

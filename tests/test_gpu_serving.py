@@ -1,0 +1,101 @@
+"""Served form (rewl_server_*): requests of different models and sizes are
+admitted by slots and device memory and run together; every result must be
+bit-identical to the same request solved alone with rewl_create/rewl_step."""
+import numpy as np
+import pytest
+
+from paper_1305_5615_gb300 import rewl
+
+pytestmark = pytest.mark.gpu
+
+REQS = [dict(model="ising", L=8, windows=4, walkers_per_window=2, lnf_final=1e-4, seed=11, q=2),
+        dict(model="potts", L=6, windows=3, walkers_per_window=2, lnf_final=1e-3, seed=12, q=3),
+        dict(model="ea", L=8, windows=4, walkers_per_window=2, lnf_final=1e-3, seed=13, q=2)]
+
+
+def _alone(r):
+    D = rewl.REWL(r["model"], r["L"], r["windows"], 0.75, r["walkers_per_window"], 0.8, r["lnf_final"], r["seed"],
+                  q=r["q"])
+    assert D.step(0)   # runs to completion
+    return D.lng(), D.info["sweep_clock"]
+
+
+def _submit(S, r):
+    return S.submit(r["model"], r["L"], r["windows"], 0.75, r["walkers_per_window"], 0.8, r["lnf_final"], r["seed"],
+                    q=r["q"])
+
+
+def test_results_in_the_mix_equal_results_alone():
+    alone = [_alone(r) for r in REQS]
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=2)   # two slots: the third request waits
+    ids = [_submit(S, r) for r in REQS]
+    assert S.poll(ids[2])["state"] == rewl.REQ_QUEUED
+    for _ in range(100000):
+        st = S.run(50)
+        if st["finished"] + st["failed"] == len(REQS):
+            break
+    assert st["finished"] == len(REQS) and st["failed"] == 0
+    for rid, ((g, e0, de), sweeps) in zip(ids, alone):
+        info = S.poll(rid)
+        assert info["state"] == rewl.REQ_DONE and info["sweeps"] == sweeps
+        gm, e0m, dem = S.result(rid)
+        assert (e0m, dem) == (e0, de)
+        assert np.array_equal(gm.view(np.uint64), g.view(np.uint64))   # bit-identical
+        assert info["latency_ms"] >= info["run_ms"] >= 0 and info["queued_ms"] >= 0
+
+
+def test_admission_by_device_memory():
+    probe = rewl.RewlServer(device_bytes=1 << 30, max_running=8)
+    rid = _submit(probe, REQS[0])
+    need = probe.poll(rid)["device_bytes"]
+    probe.close()
+    S = rewl.RewlServer(device_bytes=need + need // 2, max_running=8)   # memory for one request at a time
+    ids = [_submit(S, REQS[0]) for _ in range(3)]
+    st = S.run(1)
+    assert st["running"] == 1 and st["queued"] == 2 and st["device_bytes_in_use"] == need
+    for _ in range(100000):
+        st = S.run(50)
+        if st["finished"] == 3:
+            break
+    assert st["finished"] == 3 and st["device_bytes_in_use"] == 0
+    res = [S.result(i)[0] for i in ids]
+    assert all(np.array_equal(res[0].view(np.uint64), r.view(np.uint64)) for r in res)   # same seed, same result
+    with pytest.raises(rewl.RewlError) as e:
+        rewl.RewlServer(device_bytes=need // 2, max_running=8).submit("ising", 8, 4, 0.75, 2, 0.8, 1e-4, 1)
+    assert e.value.status == 2
+
+
+def test_cancel_leaves_others_unchanged():
+    (g0, _, _), _ = _alone(REQS[0])
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=4)
+    a = _submit(S, REQS[0])
+    b = _submit(S, REQS[1])
+    c = _submit(S, REQS[2])
+    S.run(3)
+    S.cancel(b)
+    S.cancel(c)
+    assert S.poll(b)["state"] == rewl.REQ_CANCELLED and S.poll(c)["state"] == rewl.REQ_CANCELLED
+    for _ in range(100000):
+        st = S.run(50)
+        if st["running"] == 0 and st["queued"] == 0:
+            break
+    assert S.poll(a)["state"] == rewl.REQ_DONE
+    assert np.array_equal(S.result(a)[0].view(np.uint64), g0.view(np.uint64))
+    with pytest.raises(rewl.RewlError) as e:
+        S.result(b)
+    assert e.value.status == 7
+
+
+def test_bad_requests():
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=2)
+    with pytest.raises(rewl.RewlError):
+        S.submit("ising", 8, 4, 1.5, 2, 0.8, 1e-4, 1)
+    with pytest.raises(rewl.RewlError):
+        S.submit("ising", 300, 4, 0.75, 2, 0.8, 1e-4, 1)
+    # fails at admission (windows narrower than 3 bins), reported as a failed request
+    rid = S.submit("ising", 8, 200, 0.75, 1, 0.8, 1e-4, 1)
+    S.run(1)
+    assert S.poll(rid)["state"] == rewl.REQ_FAILED and S.poll(rid)["error"] == 1
+    with pytest.raises(rewl.RewlError) as e:
+        S.poll(999999)
+    assert e.value.status == 8
