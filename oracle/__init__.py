@@ -28,6 +28,7 @@ _lib = None
 
 ISING, POTTS, EA = 0, 1, 2
 MODEL_NAMES = {"ising": ISING, "potts": POTTS, "ea": EA}
+WL_RULES = {"flat": 0, "1/t": 1}
 
 
 def build(force=False):
@@ -48,7 +49,7 @@ def build(force=False):
 class _Params(ctypes.Structure):
     _fields_ = [("sweeps_per_exchange", ctypes.c_int), ("sweeps_per_flat_check", ctypes.c_int),
                 ("lnf0", ctypes.c_double), ("entry_max_sweeps", ctypes.c_int),
-                ("discovery_sweeps", ctypes.c_int)]
+                ("discovery_sweeps", ctypes.c_int), ("wl_rule", ctypes.c_int)]
 
 
 def lib():
@@ -66,6 +67,9 @@ def lib():
         L.orc_run_blocks.restype = ctypes.c_int
         L.orc_info.argtypes = [P, P]
         L.orc_get_windows.argtypes = [P, P, P, P, P]
+        L.orc_get_phase.argtypes = [P, P]
+        L.orc_walker_all_seen.argtypes = [P, ctypes.c_int]
+        L.orc_walker_all_seen.restype = ctypes.c_int
         L.orc_get_walkers.argtypes = [P, P, P, P, P]
         L.orc_get_couplings.argtypes = [P, P]
         L.orc_get_counters.argtypes = [P, P, P, P, P]
@@ -99,11 +103,13 @@ class OracleREWL:
 
     def __init__(self, model, L, windows, overlap, walkers_per_window, flatness, lnf_final, seed, q=2,
                  couplings=None, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
-                 entry_max_sweeps=1000, discovery_sweeps=200):
+                 entry_max_sweeps=1000, discovery_sweeps=200, wl_rule=0):
         if isinstance(model, str):
             model = MODEL_NAMES[model]
+        if isinstance(wl_rule, str):
+            wl_rule = WL_RULES[wl_rule]
         self._lib = lib()
-        p = _Params(sweeps_per_exchange, sweeps_per_flat_check, lnf0, entry_max_sweeps, discovery_sweeps)
+        p = _Params(sweeps_per_exchange, sweeps_per_flat_check, lnf0, entry_max_sweeps, discovery_sweeps, wl_rule)
         h = ctypes.c_void_p()
         cpl = None
         if couplings is not None:
@@ -145,8 +151,10 @@ class OracleREWL:
         lnf = np.zeros(h, np.float64)
         it = np.zeros(h, np.int32)
         done = np.zeros(h, np.int32)
+        phase = np.zeros(h, np.int32)
         self._lib.orc_get_windows(self._h, _ptr(start), _ptr(lnf), _ptr(it), _ptr(done))
-        return {"start": start, "lnf": lnf, "iteration": it, "done": done}
+        self._lib.orc_get_phase(self._h, _ptr(phase))
+        return {"start": start, "lnf": lnf, "iteration": it, "done": done, "phase": phase}
 
     def walkers(self):
         n = self.h * self.m
@@ -174,6 +182,9 @@ class OracleREWL:
     def energy(self, spins):
         s = np.ascontiguousarray(spins, dtype=np.uint8)
         return int(self._lib.orc_energy(self._h, _ptr(s)))
+
+    def walker_all_seen(self, W):
+        return bool(self._lib.orc_walker_all_seen(self._h, W))
 
     def walker_is_flat(self, W):
         return bool(self._lib.orc_walker_is_flat(self._h, W))

@@ -243,6 +243,7 @@ void orc_default_params(orc_params* p) {
   p->lnf0 = 1.0;
   p->entry_max_sweeps = 1000;
   p->discovery_sweeps = 200;
+  p->wl_rule = 0;
 }
 
 int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings, int h, double overlap, int m,
@@ -255,7 +256,8 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   if (model == ORC_EA && (L % 2) != 0) return ORC_EINVAL;
   if (!(overlap > 0.0 && overlap < 1.0) || !(flatness > 0.0 && flatness <= 1.0) || !(lnf_final > 0.0)) return ORC_EINVAL;
   if (!(P.lnf0 >= lnf_final) || P.sweeps_per_exchange < 1 || P.sweeps_per_flat_check < P.sweeps_per_exchange ||
-      P.sweeps_per_flat_check % P.sweeps_per_exchange != 0 || P.entry_max_sweeps < 1 || P.discovery_sweeps < 0)
+      P.sweeps_per_flat_check % P.sweeps_per_exchange != 0 || P.entry_max_sweeps < 1 || P.discovery_sweeps < 0 ||
+      (P.wl_rule != 0 && P.wl_rule != 1))
     return ORC_EINVAL;
   if (model != ORC_EA && couplings != NULL) return ORC_EINVAL;
 
@@ -297,6 +299,7 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   R->lnf = (double*)calloc((size_t)h, sizeof(double));
   R->iter = (int*)calloc((size_t)h, sizeof(int));
   R->done = (int*)calloc((size_t)h, sizeof(int));
+  R->phase = (int*)calloc((size_t)h, sizeof(int));
   R->wl_accept = (uint64_t*)calloc((size_t)n_walkers, sizeof(uint64_t));
   R->near_ties = (uint64_t*)calloc((size_t)n_walkers, sizeof(uint64_t));
   R->x_tried = (uint64_t*)calloc((size_t)h, sizeof(uint64_t));
@@ -349,7 +352,7 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
 void orc_destroy(orc_rewl* R) {
   if (!R) return;
   free(R->Jr); free(R->Jd); free(R->spins); free(R->E); free(R->entry_t); free(R->seed_config);
-  free(R->win_start); free(R->lnf); free(R->iter); free(R->done); free(R->lng); free(R->H);
+  free(R->win_start); free(R->lnf); free(R->iter); free(R->done); free(R->phase); free(R->lng); free(R->H);
   free(R->wl_accept); free(R->near_ties); free(R->x_tried); free(R->x_accepted);
   free(R);
 }
@@ -475,10 +478,10 @@ int orc_walker_is_flat(const orc_rewl* R, int W) {
   return (double)hmin * (double)n >= R->flatness * (double)S;
 }
 
-static void flatness_and_merge(orc_rewl* R, int a) {
+/* The m estimators of window a are averaged (mean of ln g, summed in walker */
+/* order) and handed back to all of them; H is reset.                        */
+static void merge_window(orc_rewl* R, int a) {
   int m = R->m;
-  for (int k = 0; k < m; ++k)
-    if (!orc_walker_is_flat(R, a * m + k)) return;
   for (int b = 0; b < R->w; ++b) {
     double sum = lng_of(R, a * m)[b];
     for (int k = 1; k < m; ++k) sum = sum + lng_of(R, a * m + k)[b];
@@ -488,9 +491,71 @@ static void flatness_and_merge(orc_rewl* R, int a) {
       H_of(R, a * m + k)[b] = 0u;
     }
   }
-  R->lnf[a] = R->lnf[a] * 0.5; /* f -> sqrt(f) */
   R->iter[a] += 1;
+}
+
+static void halve_lnf(orc_rewl* R, int a) {
+  R->lnf[a] = R->lnf[a] * 0.5; /* f -> sqrt(f) */
   if (R->lnf[a] < R->lnf_final) R->done[a] = 1; /* this window reached f_final */
+}
+
+static void flatness_and_merge(orc_rewl* R, int a) {
+  int m = R->m;
+  for (int k = 0; k < m; ++k)
+    if (!orc_walker_is_flat(R, a * m + k)) return;
+  merge_window(R, a);
+  halve_lnf(R, a);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The 1/t rule (Belardinelli and Pereyra, PRE 75, 046701 (2007)), which    */
+/* the paper names as one of the WL rules replica exchange works with.  In  */
+/* its first stage ln f is halved whenever every energy has been visited    */
+/* again (H(E) > 0 everywhere); once a halving would take ln f below 1/t,   */
+/* ln f follows 1/t, where t is the Monte Carlo time in trials per energy   */
+/* level.  Reading used here (the paper gives no details):                  */
+/*   - t of window a = (trials per walker) / w = sweep_clock * N / w;       */
+/*   - stage 0 test at each check: every walker of the window has H > 0 in  */
+/*     every bin it has visited (ln g > 0); then the window merges and      */
+/*     either halves ln f = 2^-k, or, when 2^-(k+1) < 1/t (i.e.             */
+/*     sweep_clock*N < w*2^(k+1)), keeps ln f and enters stage 1;           */
+/*   - stage 1: ln f stays a power of two and follows 1/t from above: at a  */
+/*     check where t >= 2^(k+1) the window merges and halves ln f, so       */
+/*     1/t <= ln f < 2/t at every check (one halving per check at most);    */
+/*   - termination as in the flatness rule: ln f < ln f_final.              */
+/* Keeping ln f a power of two keeps every ln g exact (merge paragraph).    */
+/* ------------------------------------------------------------------------ */
+int orc_walker_all_seen(const orc_rewl* R, int W) {
+  const double* lng = R->lng + (size_t)W * R->w;
+  const uint32_t* H = R->H + (size_t)W * R->w;
+  int n = 0;
+  for (int b = 0; b < R->w; ++b) {
+    if (lng[b] > 0.0) {
+      ++n;
+      if (H[b] == 0u) return 0;
+    }
+  }
+  return n > 0;
+}
+
+static void one_over_t_step(orc_rewl* R, int a) {
+  int m = R->m;
+  int e2;
+  frexp(R->lnf[a], &e2);               /* ln f = 0.5 * 2^e2 = 2^-k */
+  int k = 1 - e2;
+  uint64_t trials = R->sweep_clock * (uint64_t)R->N;
+  /* w * 2^(k+1): t >= 2^(k+1) iff trials >= next (beyond 2^47 trials per level: never) */
+  uint64_t next = k + 1 < 48 ? (uint64_t)R->w << (k + 1) : UINT64_MAX;
+  if (R->phase[a] == 0) {
+    for (int j = 0; j < m; ++j)
+      if (!orc_walker_all_seen(R, a * m + j)) return;
+    merge_window(R, a);
+    if (trials < next) R->phase[a] = 1; /* 2^-(k+1) < 1/t: follow 1/t from here */
+    else halve_lnf(R, a);
+  } else if (trials >= next) {
+    merge_window(R, a);
+    halve_lnf(R, a);
+  }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -517,8 +582,11 @@ int orc_run_blocks(orc_rewl* R, int64_t n_blocks, int* all_done) {
       if (!R->done[a] && !R->done[a + 1]) exchange_pair(R, a, R->xround);
     R->xround += 1u;
     if (R->sweep_clock % (uint64_t)R->params.sweeps_per_flat_check == 0)
-      for (int a = 0; a < h; ++a)
-        if (!R->done[a]) flatness_and_merge(R, a);
+      for (int a = 0; a < h; ++a) {
+        if (R->done[a]) continue;
+        if (R->params.wl_rule == 1) one_over_t_step(R, a);
+        else flatness_and_merge(R, a);
+      }
   }
   int d = 1;
   for (int a = 0; a < h; ++a) d &= R->done[a];
@@ -543,6 +611,10 @@ void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* it
     if (iter) iter[a] = R->iter[a];
     if (done) done[a] = R->done[a];
   }
+}
+
+void orc_get_phase(const orc_rewl* R, int32_t* phase) {
+  for (int a = 0; a < R->h; ++a) phase[a] = R->phase[a];
 }
 
 void orc_get_walkers(const orc_rewl* R, uint8_t* spins, int32_t* E, double* lng, uint32_t* H) {

@@ -16,6 +16,7 @@ typedef struct {
   double lnf0;                /* initial ln f (1.0) */
   int entry_max_sweeps;       /* budget of each greedy entry walk (1000 sweeps) */
   int discovery_sweeps;       /* +-J only: zero-temperature descent that fixes the energy range (200) */
+  int wl_rule;                /* 0: flatness rule (f -> sqrt f on flat H); 1: the 1/t rule */
 } orc_params;
 
 typedef struct orc_rewl {
@@ -29,6 +30,7 @@ typedef struct orc_rewl {
   int* win_start;             /* first global bin of each window */
   double* lnf;
   int *iter, *done;
+  int* phase;                 /* 1/t rule: 0 while ln f is halved on the histogram test, 1 once it follows 1/t */
   uint8_t* spins;             /* [h*m][N] */
   int* E;                     /* [h*m] */
   double* lng;                /* [h*m][w] */
@@ -50,6 +52,8 @@ int orc_energy(const orc_rewl* R, const uint8_t* s);
 int orc_walker_is_flat(const orc_rewl* R, int W);
 void orc_info(const orc_rewl* R, int64_t* info);
 void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* iter, int32_t* done);
+void orc_get_phase(const orc_rewl* R, int32_t* phase);
+int orc_walker_all_seen(const orc_rewl* R, int W);
 void orc_get_walkers(const orc_rewl* R, uint8_t* spins, int32_t* E, double* lng, uint32_t* H);
 void orc_get_couplings(const orc_rewl* R, int8_t* J);
 void orc_get_counters(const orc_rewl* R, uint64_t* wl_accept, uint64_t* near_ties, uint64_t* x_tried,
