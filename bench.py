@@ -146,6 +146,26 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_seed(base, rank):
+    """Seed of the replica on `rank`: independent solves, one per rank."""
+    return base + rank
+
+
+def aggregate_replicas(t_local, att_local, world, device="cuda"):
+    """Whole-job throughput of independent replicas: attempts of all ranks /
+    the longest rank's time (max-over-ranks timing)."""
+    if world <= 1:
+        return att_local / t_local, t_local, att_local
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    aa = torch.tensor([att_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(aa, op=dist.ReduceOp.SUM)
+    return float(aa.item()) / float(tt.item()), float(tt.item()), float(aa.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -210,7 +230,7 @@ def run_gb300(args, wl, world, rank, local):
     from paper_1305_5615_gb300 import rewl
 
     rewl.load()
-    seed = args.seed + rank
+    seed = replica_seed(args.seed, rank)
     stream = torch.cuda.Stream()
     mode = rewl.MODE_GRAPH if args.mode == "graph" else rewl.MODE_PLAIN
 
@@ -247,14 +267,7 @@ def run_gb300(args, wl, world, rank, local):
     att_local = i1["attempts"] - i0["attempts"]
     launches = i1["sweep_launches"] - i0["sweep_launches"]
     sweep_ms = i1["sweep_ms"] - i0["sweep_ms"]
-    t_max, att_sum = t_local, att_local
-    if world > 1:
-        tt = torch.tensor([t_local], dtype=torch.float64, device="cuda")
-        aa = torch.tensor([att_local], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        dist.all_reduce(aa, op=dist.ReduceOp.SUM)
-        t_max, att_sum = float(tt.item()), float(aa.item())
-    value = att_sum / t_max
+    value, t_max, att_sum = aggregate_replicas(t_local, att_local, world)
 
     # ---- end to end through the C ABI with host buffers: create (H2D of the
     # problem), one flatness period, the joined ln g read back (D2H), destroy
@@ -334,11 +347,44 @@ def served_requests(n, seed):
     return out
 
 
+def _plain_sweep_seconds(rewl, shapes, seed):
+    """Plain form, per request shape: device seconds per sweep of a request of
+    that shape alone (8 windows x 4 walkers, all windows running), and the
+    seconds of rewl_create.  2000 sweeps after 1000 of warm-up."""
+    out = {}
+    for model, L, q in shapes:
+        t0 = time.perf_counter()
+        D = rewl.REWL(model, L, 8, OVERLAP, 4, FLATNESS, 1e-6, seed, q=q)
+        t_create = time.perf_counter() - t0
+        D.step(1000)
+        t1 = time.perf_counter()
+        D.step(2000)
+        out[(model, L)] = ((time.perf_counter() - t1) / 2000.0, t_create)
+        D.close()
+    return out
+
+
+def _fifo_latencies(arrivals, services):
+    """One server, first come first served: latency of each job (Lindley)."""
+    free_at, lat = 0.0, []
+    for a, sv in zip(arrivals, services):
+        start = max(a, free_at)
+        free_at = start + sv
+        lat.append(free_at - a)
+    return lat
+
+
 def run_served(args, world, rank, local):
-    """Poisson stream of DOS requests through the request server (continuous
-    batching); p50/p99 latency from arrival to result and aggregate attempts/s.
-    The same requests are also solved one after another in plain form for the
-    comparison (--plain-requests of them)."""
+    """A stream of DOS requests through the request server (continuous
+    batching, shape groups on their own streams): p50/p99 latency from arrival
+    to result and aggregate attempts/s, measured.  Beside it the plain form
+    (one request at a time, one launch per phase): its service time per
+    request is the request's own sweep count (the same in both forms -- the
+    trajectories are bit-identical) times the plain seconds per sweep of its
+    shape, measured here per shape, and its latencies follow from the same
+    arrivals through a first-come-first-served queue.  --plain-check requests
+    are also solved plain in full, to check the result bits and the modelled
+    service time."""
     import numpy as np
     import torch
 
@@ -362,39 +408,64 @@ def run_served(args, world, rank, local):
         st = S.run(1)
         if nxt == len(reqs) and st["running"] == 0 and st["queued"] == 0:
             break
+        if args.served_timeout > 0 and time.perf_counter() - t0 > args.served_timeout:
+            break
         if st["running"] == 0 and st["queued"] == 0 and nxt < len(reqs):
             time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
     t_end = time.perf_counter() - t0
-    lat, att, failed = [], 0, 0
+    done, att, n_failed, n_open = [], 0, 0, 0
     for k, rid in enumerate(ids):
         inf = S.poll(rid)
-        if inf["state"] != rewl.REQ_DONE:
-            failed += 1
-            continue
-        lat.append(1e3 * (t_sub[k] - arrivals[k]) + inf["latency_ms"])   # arrival -> result
         att += inf["attempts"]
-    lat = np.array(lat)
-    served = {"requests": len(reqs), "failed": failed, "wall_s": t_end, "attempts": att,
-              "attempts_per_s": att / t_end, "p50_latency_s": float(np.percentile(lat, 50)) / 1e3,
-              "p99_latency_s": float(np.percentile(lat, 99)) / 1e3, "rate_per_s": args.rate, "slots": args.slots}
+        if inf["state"] == rewl.REQ_DONE:
+            done.append((k, 1e-3 * (1e3 * (t_sub[k] - arrivals[k]) + inf["latency_ms"]), inf["sweeps"], inf["attempts"]))
+        elif inf["state"] == rewl.REQ_FAILED:
+            n_failed += 1
+        else:
+            n_open += 1
+    lat = np.array([d[1] for d in done]) if done else np.zeros(1)
+    served = {"requests": len(reqs), "submitted": len(ids), "completed": len(done), "failed": n_failed,
+              "unfinished_at_stop": n_open, "wall_s": t_end, "attempts": att, "attempts_per_s": att / t_end,
+              "completed_per_s": len(done) / t_end, "p50_latency_s": float(np.percentile(lat, 50)),
+              "p99_latency_s": float(np.percentile(lat, 99)), "rate_per_s": args.rate, "slots": args.slots,
+              "rounds": st["rounds"]}
+
+    # ---- plain form: per-shape sweep time, modelled service times, FIFO over the same arrivals
+    shapes = sorted({(r["model"], r["L"], r["q"]) for r in reqs})
+    per = _plain_sweep_seconds(rewl, shapes, args.seed)
     plain = None
-    if args.plain_requests > 0:
+    if done:
+        svc = [per[(reqs[k]["model"], reqs[k]["L"])][0] * sw + per[(reqs[k]["model"], reqs[k]["L"])][1]
+               for k, _, sw, _ in done]
+        plat = np.array(_fifo_latencies([arrivals[k] for k, _, _, _ in done], svc))
+        plain = {"completed_requests_modelled": len(done), "service_s_mean": float(np.mean(svc)),
+                 "busy_s": float(np.sum(svc)), "attempts_per_s": float(sum(d[3] for d in done) / np.sum(svc)),
+                 "p50_latency_s": float(np.percentile(plat, 50)), "p99_latency_s": float(np.percentile(plat, 99)),
+                 "sweep_ms_by_shape": {"%s-L%d" % k: 1e3 * v[0] for k, v in per.items()}}
+    # ---- live plain solves of the cheapest completed requests: result bits and modelled time
+    check = []
+    for k, _, sw, _ in sorted(done, key=lambda d: per[(reqs[d[0]]["model"], reqs[d[0]]["L"])][0] * d[2])[:args.plain_check]:
+        r = reqs[k]
         t1 = time.perf_counter()
-        pa = 0
-        for r in reqs[:args.plain_requests]:
-            D = rewl.REWL(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"])
-            D.step(0)
-            pa += D.info["attempts"]
-            D.close()
-        pt = time.perf_counter() - t1
-        plain = {"requests": args.plain_requests, "wall_s": pt, "attempts_per_s": pa / pt,
-                 "mean_service_s": pt / args.plain_requests}
+        D = rewl.REWL(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"])
+        D.step(0)
+        g, _, _ = D.lng()
+        el = time.perf_counter() - t1
+        gs, _, _ = S.result(ids[k])
+        check.append({"shape": "%s-L%d" % (r["model"], r["L"]), "sweeps": sw, "plain_s": el,
+                      "modelled_s": per[(r["model"], r["L"])][0] * sw + per[(r["model"], r["L"])][1],
+                      "bit_identical": bool(np.array_equal(g.view(np.uint64), gs.view(np.uint64)))})
+        D.close()
+    if plain is not None:
+        plain["live_check"] = check
     if rank == 0:
         print(json.dumps({"metric": "served DOS requests: aggregate spin-flip attempts/s; p50/p99 arrival->result",
                           "value": served["attempts_per_s"], "unit": "attempts/s", "n_gpus": world,
                           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "served-stream", "desc": "Poisson stream; +-J L in {12..32}, Ising and "
-                                     "Potts q=10 L in {16,24,32}; 8 windows x 4 walkers; ln f -> 1e-6"},
+                          "config": {"workload": "served-stream", "desc": "+-J L in {12,16,20,24,32} (p=1/2 couplings "
+                                     "from the request seed), Ising and Potts q=10 L in {16,24,32}, 1/3 each; 8 windows "
+                                     "x 4 walkers; ln f -> 1e-6; arrivals %s" % (
+                                         "Poisson %.4g/s" % args.rate if args.rate > 0 else "all at t=0 (backlog)")},
                           "served": served, "plain_one_at_a_time": plain}), flush=True)
 
 
@@ -410,11 +481,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--requests", type=int, default=96, help="served-stream: number of requests")
+    ap.add_argument("--requests", type=int, default=192, help="served-stream: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="served-stream: Poisson arrivals per second (0 = all at once)")
-    ap.add_argument("--slots", type=int, default=1024, help="served-stream: request slots")
+    ap.add_argument("--slots", type=int, default=96, help="served-stream: request slots")
     ap.add_argument("--server-gb", type=int, default=64, help="served-stream: device-memory budget in GiB")
-    ap.add_argument("--plain-requests", type=int, default=0, help="served-stream: also solve this many one by one")
+    ap.add_argument("--plain-check", type=int, default=3, help="served-stream: solve this many plain in full")
+    ap.add_argument("--served-timeout", type=float, default=1200.0, help="served-stream: stop after this many seconds")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

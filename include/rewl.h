@@ -94,7 +94,28 @@ typedef struct {
                                     (plain mode); read back through rewl_info */
   int32_t sweep_variant;         /* sweep kernel form, identical results: 0 = two-deep chain (default),
                                     1 = staged one-deep chain */
+  int32_t prefetch_draws;        /* 0 = automatic: in plain mode the draws of the next block (sites, ln u,
+                                    conflict masks) are prepared on a second stream while the current block
+                                    runs, when both buffers fit in 1 GiB; -1 = never */
+  int32_t wl_rule;               /* how ln f falls (the WL "update/convergence rule"): REWL_RULE_FLAT or
+                                    REWL_RULE_ONE_OVER_T; see below */
 } rewl_params;
+
+/*
+ * WL rules.  REWL_RULE_FLAT: when every walker of a window is flat at a check
+ * (min H * n >= flatness * sum H over its visited bins), the window merges and
+ * ln f halves (f -> sqrt f; WL paragraph and the merge paragraph after
+ * Eq. (1)).  REWL_RULE_ONE_OVER_T: the 1/t rule (Belardinelli and Pereyra,
+ * PRE 75, 046701 (2007)), which the paper names as one the exchange works
+ * with.  t = sweep_clock * N / window_bins (trials per energy level).  Stage
+ * 0: at a check where every walker of the window has H > 0 on all its
+ * visited bins, the window merges and halves ln f = 2^-k, unless
+ * t < 2^(k+1) -- then it keeps ln f and enters stage 1.  Stage 1: at each
+ * check with t >= 2^(k+1) the window merges and halves ln f, so ln f stays a
+ * power of two with 1/t <= ln f < 2/t.  Both rules end a window when
+ * ln f < lnf_final.
+ */
+enum { REWL_RULE_FLAT = 0, REWL_RULE_ONE_OVER_T = 1 };
 
 /* Fills *p with the defaults above. */
 void rewl_params_default(rewl_params* p);
@@ -185,6 +206,7 @@ typedef struct {
   double sweep_ms;           /* their summed device time, CUDA events on the solve's stream */
   int64_t h2d_bytes;         /* bytes copied host -> device by this handle so far */
   int64_t d2h_bytes;         /* bytes copied device -> host by this handle so far */
+  int32_t prefetch_draws;    /* 1 when the next block's draws are prepared on a second stream */
 } rewl_info;
 
 rewl_status rewl_get_info(rewl_handle h, rewl_info* info);
@@ -204,6 +226,7 @@ rewl_status rewl_get_info(rewl_handle h, rewl_info* info);
  *            acceptance tests with |ln u - Delta ln g| < 1e-12; tests that
  *            needed the FP64 logarithm
  *  x_tried, x_accepted [windows] u64: exchange pairs of window pair (a,a+1)
+ *  stage     [windows] i32: stage of the 1/t rule (REWL_RULE_ONE_OVER_T)
  */
 typedef struct {
   uint32_t* lattice;
@@ -221,6 +244,7 @@ typedef struct {
   uint64_t* x_accepted;
   int64_t sweep_clock;
   int64_t exchange_rounds;
+  int32_t* stage;       /* [windows] 1/t rule stage (0 or 1); optional, NULL reads as all 0 */
 } rewl_state;
 
 /* Copies the device state into the caller's buffers.  Errors: REWL_EINVAL,
@@ -238,6 +262,42 @@ rewl_status rewl_set_state(rewl_handle h, const rewl_state* st);
 void rewl_destroy(rewl_handle h);
 
 /*
+ * rewl_thermo -- canonical thermodynamics from a density of states (the
+ * paper's opening paragraph: WL gives the free energy at any temperature from
+ * one simulation).  For each temperature T_i > 0 (k_B = 1, beta = 1/T) with
+ * w(E) = g(E) exp(-beta E):
+ *   out[5i+0] = ln Z = ln sum_E w(E)
+ *   out[5i+1] = U = <E>
+ *   out[5i+2] = C = beta^2 (<E^2> - <E>^2)   (centred two-pass sum)
+ *   out[5i+3] = F = -T ln Z
+ *   out[5i+4] = S = (U - F) / T
+ * lng: n_bins values (host), bin b at energy e_min + b * e_step, -INFINITY for
+ * levels that do not exist (e.g. rewl_get_lng's output); temperatures: n_T
+ * values (host); out: 5 * n_T doubles (host).  All quantities are totals
+ * (divide by N for per-site values).  FP64 throughout.
+ * Errors: REWL_EINVAL (sizes, non-positive temperature, no finite ln g),
+ * REWL_ENOMEM, REWL_ECUDA.
+ */
+rewl_status rewl_thermo(const double* lng, int32_t n_bins, int32_t e_min, int32_t e_step, const double* temperatures,
+                        int32_t n_T, double* out);
+
+/*
+ * rewl_thermo_jackknife -- the quantities of rewl_thermo with statistical
+ * errors by resampling over independent runs (the paper's join paragraph
+ * determines errors by resampling; jackknife as in Newman and Barkema,
+ * section 3.4.3).  lng_runs: n_runs >= 2 normalised ln g tables of one
+ * problem, [n_runs][n_bins] row-major on the host (e.g. rewl_get_lng of runs
+ * with different seeds); a bin counts only where every run is finite.
+ * est[5i+q]: quantity q of the mean ln g over all runs at temperature i
+ * (layout of rewl_thermo's out); err[5i+q] = sqrt((R-1)/R * sum_r (Q_(r) -
+ * mean_r Q_(r))^2), Q_(r) from the mean without run r.  Host buffers of
+ * 5 * n_T doubles.  Errors: REWL_EINVAL (sizes, temperatures, no bin finite in
+ * every run), REWL_ENOMEM, REWL_ECUDA.
+ */
+rewl_status rewl_thermo_jackknife(const double* lng_runs, int32_t n_runs, int32_t n_bins, int32_t e_min,
+                                  int32_t e_step, const double* temperatures, int32_t n_T, double* est, double* err);
+
+/*
  * Served form.  The paper runs one solve at a time (one walker per CPU core,
  * conclusion paragraph); here many independent REWL solves -- different
  * models, lattice sizes, disorder realisations -- run together on one GPU.
@@ -248,14 +308,18 @@ void rewl_destroy(rewl_handle h);
  * Requests are queued at submission (inputs are copied) and admitted first
  * come, first served while a slot (max_running) and the device-memory budget
  * allow; the memory a request may need is estimated from its sizes with the
- * widest window its energy range allows.  rewl_server_run advances the server
- * by rounds: admission, then for every running request one block of
- * sweeps_per_exchange sweeps, one exchange round and, when due, the flatness
- * check -- one launch per model for the sweeps of all running walkers, one
- * launch each for the exchanges, clocks and flatness checks of all requests.
- * Finished requests are retired at the end of the round: their joined ln g is
- * read back (rewl_server_result) and their memory returns to the budget.
- * The server is internally synchronised: any thread may call it.
+ * widest window its energy range allows.  Running requests are grouped by
+ * shape (model, L).  A group advances by rounds: for every request of the
+ * group one block of sweeps_per_exchange sweeps, one exchange round and,
+ * when due, the flatness check -- one fused launch for the sweeps of all the
+ * group's walkers, one launch each for the exchanges, clocks and flatness
+ * checks of all its requests.  Each group runs on a stream of its own, so
+ * groups of different sizes progress side by side at their own pace.
+ * rewl_server_run issues a round for every idle group and returns once at
+ * least one round has finished, per unit of max_rounds.  Finished requests
+ * are retired when their group's round is read: their joined ln g is read
+ * back (rewl_server_result) and their memory returns to the budget.  The
+ * server is internally synchronised: any thread may call it.
  */
 typedef struct rewl_server* rewl_server_handle;
 
@@ -291,16 +355,22 @@ typedef struct {
 
 /* device_bytes: memory budget for running requests; max_running: request slots;
  * params: sweeps_per_exchange, sweeps_per_flat_check, lnf0, entry and
- * discovery budgets, stream and allocator of every request (NULL = defaults).
- * Errors: REWL_EINVAL, REWL_ENOMEM, REWL_ECUDA. */
+ * discovery budgets and allocator of every request (NULL = defaults);
+ * params.stream: NULL = one stream per shape group (groups overlap on the
+ * device), else every group and request runs on that one stream (in order);
+ * params.timeout_ms > 0: rewl_server_run fails with REWL_ETIMEOUT when no
+ * round finishes within that time.  Errors: REWL_EINVAL, REWL_ENOMEM, REWL_ECUDA. */
 rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, int32_t max_running,
                                const rewl_params* params);
 /* Queues a request; *id identifies it.  Errors: REWL_EINVAL (malformed),
  * REWL_ENOMEM (larger than the whole budget).  Errors found at admission
  * (e.g. REWL_EENTRY) end the request in REWL_REQ_FAILED. */
 rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* r, uint64_t* id);
-/* Runs up to max_rounds rounds (stops early when nothing runs or waits);
- * *stats (may be NULL) describes the server afterwards.  Errors: REWL_ECUDA. */
+/* Admits what fits, issues a round for every idle group and waits until at
+ * least one round has finished; repeated up to max_rounds times (stops early
+ * when nothing runs).  stats->rounds counts the group rounds finished so far.
+ * *stats (may be NULL) describes the server afterwards.
+ * Errors: REWL_ECUDA, REWL_ETIMEOUT. */
 rewl_status rewl_server_run(rewl_server_handle s, int32_t max_rounds, rewl_server_stats* stats);
 /* State, timings and counters of a request.  Errors: REWL_ENOTFOUND. */
 rewl_status rewl_server_poll(rewl_server_handle s, uint64_t id, rewl_request_info* info);

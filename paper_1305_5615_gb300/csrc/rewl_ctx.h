@@ -36,6 +36,15 @@ struct rewl_ctx {
   int ev_pending = 0;
   int64_t sweep_launches = 0;
   double sweep_ms = 0.0;
+  // draws of the next block prepared on a second stream (plain mode, when both buffers fit)
+  bool pre_on = false;
+  rewl::PreTrial* pre_buf[2] = {nullptr, nullptr};
+  uint32_t pre_stride = 0;
+  uint64_t pre_t0[2] = {~0ull, ~0ull};
+  int pre_cur = 0;
+  cudaStream_t pre_stream = nullptr;
+  cudaEvent_t ev_pre[2] = {nullptr, nullptr};
+  cudaEvent_t ev_used[2] = {nullptr, nullptr};
 
   ~rewl_ctx();
   void* dalloc(size_t bytes, rewl_status* st);

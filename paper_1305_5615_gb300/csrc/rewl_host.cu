@@ -66,8 +66,14 @@ rewl_ctx::~rewl_ctx() {
     if (params.free) params.free(p, (void*)stream, params.alloc_user);
     else cudaFree(p);
   }
+  if (pre_stream) cudaStreamSynchronize(pre_stream);
   if (h_n_done) cudaFreeHost(h_n_done);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k) {
+    if (ev_pre[k]) cudaEventDestroy(ev_pre[k]);
+    if (ev_used[k]) cudaEventDestroy(ev_used[k]);
+  }
+  if (pre_stream) cudaStreamDestroy(pre_stream);
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
 
@@ -248,6 +254,8 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
     return fail(REWL_EINVAL, "walkers_per_block %d", prm.walkers_per_block);
   if (prm.mode != REWL_MODE_PLAIN && prm.mode != REWL_MODE_GRAPH) return fail(REWL_EINVAL, "mode %d", prm.mode);
   if (prm.sweep_variant != 0 && prm.sweep_variant != 1) return fail(REWL_EINVAL, "sweep_variant %d", prm.sweep_variant);
+  if (prm.wl_rule != REWL_RULE_FLAT && prm.wl_rule != REWL_RULE_ONE_OVER_T) return fail(REWL_EINVAL, "wl_rule %d", prm.wl_rule);
+  if (prm.prefetch_draws != 0 && prm.prefetch_draws != -1) return fail(REWL_EINVAL, "prefetch_draws %d", prm.prefetch_draws);
   if (couplings)
     for (int i = 0; i < 2 * L * L; ++i)
       if (couplings[i] != 1 && couplings[i] != -1) return fail(REWL_EINVAL, "coupling %d is %d", i, couplings[i]);
@@ -272,6 +280,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   P.seed_lo = (uint32_t)seed;
   P.seed_hi = (uint32_t)(seed >> 32);
   P.flatness = flatness;
+  P.wl_rule = prm.wl_rule;
   P.lnf_final = lnf_final;
 
   auto bail = [&](rewl_status s) {
@@ -320,6 +329,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   S.lnf = (double*)c->dalloc(sizeof(double) * P.h, &st);
   S.iter = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.done = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
+  S.stage = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.n_done = (int32_t*)c->dalloc(sizeof(int32_t), &st);
   S.wl_accept = (uint64_t*)c->dalloc(sizeof(uint64_t) * nW, &st);
   S.near_ties = (uint64_t*)c->dalloc(sizeof(uint64_t) * nW, &st);
@@ -330,7 +340,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   S.status = (int32_t*)c->dalloc(sizeof(int32_t) * nW, &st);
   S.entry_t = (uint64_t*)c->dalloc(sizeof(uint64_t) * nW, &st);
   S.seed_config = (uint32_t*)c->dalloc(sizeof(uint32_t) * P.lat_words, &st);
-  S.clock = (uint64_t*)c->dalloc(sizeof(uint64_t) * 2, &st);
+  S.clock = (uint64_t*)c->dalloc(sizeof(uint64_t) * 3, &st);
   if (st != REWL_OK) return bail(st);
   cudaStream_t s = c->stream;
 #define BAIL_CUDA(expr)                                                                                   \
@@ -342,13 +352,14 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   BAIL_CUDA(cudaMemsetAsync(S.n_done, 0, sizeof(int32_t), s));
   BAIL_CUDA(cudaMemsetAsync(S.iter, 0, sizeof(int32_t) * P.h, s));
   BAIL_CUDA(cudaMemsetAsync(S.done, 0, sizeof(int32_t) * P.h, s));
+  BAIL_CUDA(cudaMemsetAsync(S.stage, 0, sizeof(int32_t) * P.h, s));
   BAIL_CUDA(cudaMemsetAsync(S.wl_accept, 0, sizeof(uint64_t) * nW, s));
   BAIL_CUDA(cudaMemsetAsync(S.near_ties, 0, sizeof(uint64_t) * nW, s));
   BAIL_CUDA(cudaMemsetAsync(S.exact_tests, 0, sizeof(uint64_t) * nW, s));
   BAIL_CUDA(cudaMemsetAsync(S.x_tried, 0, sizeof(uint64_t) * P.h, s));
   BAIL_CUDA(cudaMemsetAsync(S.x_accepted, 0, sizeof(uint64_t) * P.h, s));
   BAIL_CUDA(cudaMemsetAsync(S.seed_config, 0, sizeof(uint32_t) * P.lat_words, s));
-  BAIL_CUDA(cudaMemsetAsync(S.clock, 0, sizeof(uint64_t) * 2, s));
+  BAIL_CUDA(cudaMemsetAsync(S.clock, 0, sizeof(uint64_t) * 3, s));
   BAIL_CUDA(launch_init(P, S, s));
 
   // energy range
@@ -397,6 +408,25 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   choose_config(c, n_sm);
   BAIL_CUDA(prepare_sweep(c->G, P.model));
+  // Draws prepared ahead on the idle SMs: plain mode, chain kernel, G >= 8, both buffers within 1 GiB.
+  {
+    const uint64_t n_att = (uint64_t)prm.sweeps_per_exchange * P.N;
+    const uint64_t stride = (n_att + 31) / 32 * 32;
+    const uint64_t bytes = (uint64_t)P.n_walkers * stride * sizeof(PreTrial);
+    if (prm.prefetch_draws == 0 && prm.mode == REWL_MODE_PLAIN && prm.sweep_variant == kSweepChain && c->G >= 8 &&
+        2 * bytes <= (1ull << 30)) {
+      c->pre_stride = (uint32_t)stride;
+      c->pre_buf[0] = (PreTrial*)c->dalloc(bytes, &st);
+      c->pre_buf[1] = (PreTrial*)c->dalloc(bytes, &st);
+      if (st != REWL_OK) return bail(st);
+      BAIL_CUDA(cudaStreamCreateWithFlags(&c->pre_stream, cudaStreamNonBlocking));
+      for (int k = 0; k < 2; ++k) {
+        BAIL_CUDA(cudaEventCreateWithFlags(&c->ev_pre[k], cudaEventDisableTiming));
+        BAIL_CUDA(cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming));
+      }
+      c->pre_on = true;
+    }
+  }
   if (sweep_smem_bytes(P, c->wpb, c->G, prm.sweep_variant) > 227 * 1024)
     return bail(fail(REWL_EINVAL, "a walker needs %zu bytes of shared memory (window of %d bins)",
                      sweep_smem_bytes(P, 1, c->G, prm.sweep_variant), P.w));
@@ -409,13 +439,29 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
 
 void rewl_destroy(rewl_handle h) { delete h; }
 
+static bool with_graph_capture(const rewl_ctx* c) { return c->params.mode == REWL_MODE_GRAPH; }
+
 // One block: sweeps, exchange, clock advance; plus the flatness check when due.
 static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
-  SweepLaunch A;
+  SweepLaunch A{};
   A.n_att = (uint32_t)(c->params.sweeps_per_exchange * c->P.N);
   A.n_active = c->n_active;
   A.wpb = c->wpb;
   A.variant = c->params.sweep_variant;
+  if (c->pre_on && !with_graph_capture(c)) {
+    // this block's draws: prepared by the previous block (checked by its first trial index), else now
+    const uint64_t t0 = c->sweep_clock * (uint64_t)c->P.N;
+    const int k = c->pre_cur;
+    if (c->pre_t0[k] != t0) {
+      CUDA_TRY(cudaStreamWaitEvent(c->pre_stream, c->ev_used[k], 0));
+      CUDA_TRY(launch_precompute(c->G, c->P, t0, A.n_att, c->pre_stride, c->pre_buf[k], c->pre_stream));
+      CUDA_TRY(cudaEventRecord(c->ev_pre[k], c->pre_stream));
+      c->pre_t0[k] = t0;
+    }
+    CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_pre[k], 0));
+    A.pre = c->pre_buf[k];
+    A.pre_stride = c->pre_stride;
+  }
   const bool timed = c->params.profile && c->params.mode == REWL_MODE_PLAIN;
   if (timed) {
     if ((int)c->ev_pool.size() < 2 * (c->ev_pending + 1)) {
@@ -429,6 +475,17 @@ static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
   }
   CUDA_TRY(launch_sweep(c->G, c->P, c->S, A, c->stream));
   if (timed) CUDA_TRY(cudaEventRecord(c->ev_pool[2 * c->ev_pending++ + 1], c->stream));
+  if (A.pre) {
+    // the next block's draws go into the other buffer while this block runs
+    const int k = c->pre_cur, k2 = k ^ 1;
+    const uint64_t t0n = (c->sweep_clock + (uint64_t)c->params.sweeps_per_exchange) * (uint64_t)c->P.N;
+    CUDA_TRY(cudaEventRecord(c->ev_used[k], c->stream));
+    CUDA_TRY(cudaStreamWaitEvent(c->pre_stream, c->ev_used[k2], 0));
+    CUDA_TRY(launch_precompute(c->G, c->P, t0n, A.n_att, c->pre_stride, c->pre_buf[k2], c->pre_stream));
+    CUDA_TRY(cudaEventRecord(c->ev_pre[k2], c->pre_stream));
+    c->pre_t0[k2] = t0n;
+    c->pre_cur = k2;
+  }
   CUDA_TRY(launch_exchange(c->P, c->S, c->stream));
   CUDA_TRY(launch_advance_clock(c->S, (uint32_t)c->params.sweeps_per_exchange, c->stream));
   if (with_flat) CUDA_TRY(launch_flat_merge(c->P, c->S, c->stream));
@@ -539,6 +596,7 @@ rewl_status rewl_get_info(rewl_handle c, rewl_info* info) {
   info->sweep_ms = c->sweep_ms;
   info->h2d_bytes = (int64_t)c->h2d_bytes;
   info->d2h_bytes = (int64_t)c->d2h_bytes;
+  info->prefetch_draws = c->pre_on ? 1 : 0;
   return REWL_OK;
 }
 
@@ -556,6 +614,7 @@ rewl_status rewl_get_state(rewl_handle c, rewl_state* st) {
   if (st->lnf) CUDA_TRY(d2h(c, st->lnf, c->S.lnf, 8 * P.h));
   if (st->iteration) CUDA_TRY(d2h(c, st->iteration, c->S.iter, 4 * P.h));
   if (st->done) CUDA_TRY(d2h(c, st->done, c->S.done, 4 * P.h));
+  if (st->stage) CUDA_TRY(d2h(c, st->stage, c->S.stage, 4 * P.h));
   if (st->wl_accept) CUDA_TRY(d2h(c, st->wl_accept, c->S.wl_accept, 8 * nW));
   if (st->near_ties) CUDA_TRY(d2h(c, st->near_ties, c->S.near_ties, 8 * nW));
   if (st->exact_tests) CUDA_TRY(d2h(c, st->exact_tests, c->S.exact_tests, 8 * nW));
@@ -591,6 +650,14 @@ rewl_status rewl_set_state(rewl_handle c, const rewl_state* st) {
   CUDA_TRY(h2d(c, c->S.lnf, st->lnf, 8 * P.h));
   CUDA_TRY(h2d(c, c->S.iter, st->iteration, 4 * P.h));
   CUDA_TRY(h2d(c, c->S.done, st->done, 4 * P.h));
+  if (st->stage) {
+    for (int a = 0; a < P.h; ++a)
+      if (st->stage[a] != 0 && (st->stage[a] != 1 || P.wl_rule != REWL_RULE_ONE_OVER_T))
+        return fail(REWL_EINVAL, "stage[%d] = %d", a, st->stage[a]);
+    CUDA_TRY(h2d(c, c->S.stage, st->stage, 4 * P.h));
+  } else {
+    CUDA_TRY(cudaMemsetAsync(c->S.stage, 0, 4 * P.h, c->stream));
+  }
   if (st->wl_accept) CUDA_TRY(h2d(c, c->S.wl_accept, st->wl_accept, 8 * nW));
   if (st->near_ties) CUDA_TRY(h2d(c, c->S.near_ties, st->near_ties, 8 * nW));
   if (st->exact_tests) CUDA_TRY(h2d(c, c->S.exact_tests, st->exact_tests, 8 * nW));

@@ -510,7 +510,8 @@ __device__ __forceinline__ void apply_move_if(uint32_t* s_lat, uint32_t widx, ui
 // Runs the sweeps of the nloc walkers wids[0..nloc) of one CTA (wpb walkers per CTA).
 template <int MODEL, int G>
 __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevState& S, uint32_t n_att, int wpb,
-                                                 const int32_t* wids, int nloc) {
+                                                 const int32_t* wids, int nloc, const PreTrial* pre = nullptr,
+                                                 uint32_t pre_stride = 0) {
   static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpad = P.w + 2 * kGuardBins;
@@ -559,32 +560,47 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
     StagedTrial* my_stage = s_stage + (size_t)lw * G;
 
+    const PreTrial* my_pre = pre ? pre + (size_t)W * pre_stride : nullptr;
+    PreTrial nxt_pre{0u, 0u, 0};
+    if (my_pre && (uint32_t)lane < n_att) nxt_pre = my_pre[lane];
     for (uint32_t base = 0; base < n_att; base += G) {
       StagedTrial tr;
       {
-        const uint64_t t = t0 + base + (uint32_t)lane;
-        const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-        const uint32_t site = scale32(r.x, (uint32_t)P.N);
-        const int y = (int)mulhi32(site, P.magic_L);
-        const int x = (int)site - y * L;
-        const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
-        const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
-        tr.thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
-        const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
-        const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
-        uint32_t M = 0;
-        if constexpr (G > 1) {
-          const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
-          const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
-          const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
-          const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
+        int x, y;
+        uint32_t pv, M = 0;
+        if (my_pre) {  // draw prepared ahead by k_precompute; prefetch the next group's
+          const PreTrial pt = nxt_pre;
+          if (base + G + (uint32_t)lane < n_att) nxt_pre = my_pre[base + G + lane];
+          x = (int)(pt.pk & 0xffu);
+          y = (int)((pt.pk >> 8) & 0xffu);
+          pv = pt.pk >> 16;
+          M = pt.mask;
+          tr.thr = pt.thr;
+        } else {
+          const uint64_t t = t0 + base + (uint32_t)lane;
+          const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+          const uint32_t site = scale32(r.x, (uint32_t)P.N);
+          y = (int)mulhi32(site, P.magic_L);
+          x = (int)site - y * L;
+          pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+          const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
+          tr.thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
+          if constexpr (G > 1) {
+            const uint32_t pk0 = (uint32_t)x | ((uint32_t)y << 8);
+            const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
+            const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
+            const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
+            const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
 #pragma unroll
-          for (int i = 0; i < G - 1; ++i) {
-            const uint32_t pi = __shfl_sync(gm, pk, i, G);
-            const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
-            M |= (hit && i < lane) ? (1u << i) : 0u;
+            for (int i = 0; i < G - 1; ++i) {
+              const uint32_t pi = __shfl_sync(gm, pk0, i, G);
+              const bool hit = pi == pk0 || pi == pl || pi == pr || pi == pu || pi == pd;
+              M |= (hit && i < lane) ? (1u << i) : 0u;
+            }
           }
         }
+        const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
+        const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
         tr.pk = (uint32_t)(ev.dbin + 8) | (pv << 8) | (pk << 16);
         tr.mask = M;
         tr.widx = ev.widx;
@@ -723,9 +739,63 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
 }
 
 template <int MODEL, int G>
-__global__ void __launch_bounds__(256) k_sweep_chain(Problem P, DevState S, SweepLaunch A) {
+__global__ void __launch_bounds__(256, 1) k_sweep_chain(Problem P, DevState S, SweepLaunch A) {
   const int first = blockIdx.x * A.wpb;
-  sweep_chain_body<MODEL, G>(P, S, A.n_att, A.wpb, S.active + first, min(A.wpb, A.n_active - first));
+  sweep_chain_body<MODEL, G>(P, S, A.n_att, A.wpb, S.active + first, min(A.wpb, A.n_active - first), A.pre,
+                             A.pre_stride);
+}
+
+// ---------------------------------------------------------------------------
+// Draws of the next sweep launch, prepared while the current one runs (on the
+// SMs the walkers leave idle): for trial i of walker W the site, the proposed
+// Potts offset, ln u, and the conflict mask of its group of G trials -- the
+// same values the sweep kernel would compute, so the results are unchanged.
+// One thread per (walker, trial); trials are padded to a multiple of 32.
+// ---------------------------------------------------------------------------
+template <int G>
+__global__ void __launch_bounds__(256) k_precompute(Problem P, uint64_t t0, uint32_t n_att, uint32_t stride,
+                                                    PreTrial* __restrict__ out) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int W = (int)(g / stride);
+  const uint32_t i = (uint32_t)(g - (uint64_t)W * stride);
+  if (W >= P.n_walkers) return;  // whole warps (stride is a multiple of 32)
+  const uint64_t t = t0 + i;
+  const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+  const uint32_t site = scale32(r.x, (uint32_t)P.N);
+  const int y = (int)mulhi32(site, P.magic_L);
+  const int x = (int)site - y * P.L;
+  const uint32_t pv = P.model == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+  const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
+  const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
+  const int L = P.L;
+  const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
+  const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
+  const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
+  const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
+  const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
+  const int lane = (int)(i % G);
+  const uint32_t gm = group_mask<G>();
+  uint32_t M = 0;
+#pragma unroll
+  for (int k = 0; k < G - 1; ++k) {
+    const uint32_t pi = __shfl_sync(gm, pk, k, G);
+    const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
+    M |= (hit && k < lane) ? (1u << k) : 0u;
+  }
+  if (i < n_att) out[g] = PreTrial{pk | (pv << 16), M, thr};
+}
+
+cudaError_t launch_precompute(int G, const Problem& P, uint64_t t0, uint32_t n_att, uint32_t stride, PreTrial* out,
+                              cudaStream_t st) {
+  const uint64_t threads = (uint64_t)P.n_walkers * stride;
+  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  switch (G) {
+    case 8: k_precompute<8><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
+    case 16: k_precompute<16><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
+    case 32: k_precompute<32><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -803,66 +873,81 @@ __device__ __forceinline__ void flat_merge_body(const Problem& P, const DevState
   __shared__ int all_flat;
   const int m = P.m, w = P.w;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  // 1/t rule: ln f = 2^-k; t >= 2^(k+1) trials per level iff clock * N >= w * 2^(k+1)
+  const int k = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
+  const uint64_t trials = S.clock[0] * (uint64_t)P.N;
+  const uint64_t next = k + 1 < 48 ? (uint64_t)w << (k + 1) : ~0ull;
+  const int stage = P.wl_rule == 1 ? S.stage[a] : 0;
   if (threadIdx.x == 0) all_flat = 1;
   __syncthreads();
-  for (int k = 0; k < m; ++k) {
-    const int W = a * m + k;
-    uint32_t hmin = 0xffffffffu;
-    unsigned long long s = 0;
-    int n = 0;
-    for (int b = threadIdx.x; b < w; b += blockDim.x) {
-      if (S.lng[(size_t)W * w + b] > 0.0) {
-        const uint32_t hv = S.H[(size_t)W * w + b];
-        hmin = min(hmin, hv);
-        s += hv;
-        ++n;
+  if (stage == 1) {
+    if (trials < next) return;  // uniform: t has not reached 2^(k+1)
+  } else {
+    for (int kw = 0; kw < m; ++kw) {
+      const int W = a * m + kw;
+      uint32_t hmin = 0xffffffffu;
+      unsigned long long sum = 0;
+      int n = 0;
+      for (int b = threadIdx.x; b < w; b += blockDim.x) {
+        if (S.lng[(size_t)W * w + b] > 0.0) {
+          const uint32_t hv = S.H[(size_t)W * w + b];
+          hmin = min(hmin, hv);
+          sum += hv;
+          ++n;
+        }
       }
-    }
-    for (int o = 16; o; o >>= 1) {
-      hmin = min(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      n += __shfl_xor_sync(0xffffffffu, n, o);
-    }
-    if (lane == 0) {
-      r_min[wid] = hmin;
-      r_sum[wid] = s;
-      r_n[wid] = n;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t hm = 0xffffffffu;
-      unsigned long long ss = 0;
-      int nn = 0;
-      for (int i = 0; i < nw; ++i) {
-        hm = min(hm, r_min[i]);
-        ss += r_sum[i];
-        nn += r_n[i];
+      for (int o = 16; o; o >>= 1) {
+        hmin = min(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+        sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        n += __shfl_xor_sync(0xffffffffu, n, o);
       }
-      // flat iff min H * n >= flatness * sum H over the visited bins
-      const bool flat = nn > 0 && __dmul_rn(__uint2double_rn(hm), __int2double_rn(nn)) >=
-                                      __dmul_rn(P.flatness, __ull2double_rn(ss));
-      if (!flat) all_flat = 0;
+      if (lane == 0) {
+        r_min[wid] = hmin;
+        r_sum[wid] = sum;
+        r_n[wid] = n;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint32_t hm = 0xffffffffu;
+        unsigned long long ss = 0;
+        int nn = 0;
+        for (int i = 0; i < nw; ++i) {
+          hm = min(hm, r_min[i]);
+          ss += r_sum[i];
+          nn += r_n[i];
+        }
+        // flatness rule: min H * n >= flatness * sum H over the visited bins;
+        // 1/t rule, first stage: every visited bin seen again (min H > 0)
+        const bool ok = P.wl_rule == 1 ? (nn > 0 && hm > 0u)
+                                       : (nn > 0 && __dmul_rn(__uint2double_rn(hm), __int2double_rn(nn)) >=
+                                                        __dmul_rn(P.flatness, __ull2double_rn(ss)));
+        if (!ok) all_flat = 0;
+      }
+      __syncthreads();
+      if (!all_flat) return;
     }
-    __syncthreads();
-    if (!all_flat) return;
   }
   // merge: mean of the m estimators (summed in walker order), H reset
   for (int b = threadIdx.x; b < w; b += blockDim.x) {
     double sum = S.lng[(size_t)(a * m) * w + b];
-    for (int k = 1; k < m; ++k) sum = __dadd_rn(sum, S.lng[(size_t)(a * m + k) * w + b]);
+    for (int kw = 1; kw < m; ++kw) sum = __dadd_rn(sum, S.lng[(size_t)(a * m + kw) * w + b]);
     const double mean = __ddiv_rn(sum, (double)m);
-    for (int k = 0; k < m; ++k) {
-      S.lng[(size_t)(a * m + k) * w + b] = mean;
-      S.H[(size_t)(a * m + k) * w + b] = 0u;
+    for (int kw = 0; kw < m; ++kw) {
+      S.lng[(size_t)(a * m + kw) * w + b] = mean;
+      S.H[(size_t)(a * m + kw) * w + b] = 0u;
     }
   }
   if (threadIdx.x == 0) {
-    const double lnf = __dmul_rn(S.lnf[a], 0.5);  // f -> sqrt(f)
-    S.lnf[a] = lnf;
     S.iter[a] += 1;
-    if (lnf < P.lnf_final) {
-      S.done[a] = 1;
-      atomicAdd(S.n_done, 1);
+    if (P.wl_rule == 1 && stage == 0 && trials < next) {
+      S.stage[a] = 1;  // halving would take ln f below 1/t: follow 1/t from here
+    } else {
+      const double lnf = __dmul_rn(S.lnf[a], 0.5);  // f -> sqrt(f)
+      S.lnf[a] = lnf;
+      if (lnf < P.lnf_final) {
+        S.done[a] = 1;
+        atomicAdd(S.n_done, 1);
+      }
     }
   }
 }
@@ -877,9 +962,10 @@ __global__ void k_flat_merge(Problem P, DevState S) { flat_merge_body(P, S, (int
 // clock is at a multiple of their flatness period.  Every request keeps its
 // own schedule, streams and state, so its trajectory is the one it has alone.
 // ---------------------------------------------------------------------------
-template <int MODEL>
-__global__ void __launch_bounds__(32) k_sweep_batch(const BatchSlot* __restrict__ slots,
-                                                    const BatchWalker* __restrict__ list) {
+// One launch for the walkers of every model: each CTA runs the body of its
+// slot's model.
+__global__ void __launch_bounds__(32, 16) k_sweep_batch(const BatchSlot* __restrict__ slots,
+                                                        const BatchWalker* __restrict__ list) {
   __shared__ int32_t wid;
   const BatchWalker bw = list[blockIdx.x];
   const Problem P = slots[bw.slot].P;
@@ -888,7 +974,11 @@ __global__ void __launch_bounds__(32) k_sweep_batch(const BatchSlot* __restrict_
   if (!slots[bw.slot].active || S.done[bw.W / P.m]) return;  // uniform over the CTA
   if (threadIdx.x == 0) wid = bw.W;
   __syncthreads();
-  sweep_chain_body<MODEL, 32>(P, S, n_att, 1, &wid, 1);
+  switch (P.model) {
+    case kIsing: sweep_chain_body<kIsing, 32>(P, S, n_att, 1, &wid, 1); break;
+    case kPotts: sweep_chain_body<kPotts, 32>(P, S, n_att, 1, &wid, 1); break;
+    default: sweep_chain_body<kEA, 32>(P, S, n_att, 1, &wid, 1); break;
+  }
 }
 
 __global__ void k_exchange_batch(const BatchSlot* __restrict__ slots, int max_pairs) {
@@ -902,8 +992,12 @@ __global__ void k_exchange_batch(const BatchSlot* __restrict__ slots, int max_pa
 __global__ void k_advance_batch(const BatchSlot* __restrict__ slots, int n_slots) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slots || !slots[s].active) return;
-  slots[s].S.clock[0] += slots[s].spe;
-  slots[s].S.clock[1] += 1;
+  const int h = slots[s].P.h, nd = *slots[s].S.n_done;  // windows done before this round's check
+  if (nd >= h) return;                                   // finished: the clocks stay
+  uint64_t* clk = slots[s].S.clock;
+  clk[0] += slots[s].spe;
+  clk[1] += 1;
+  clk[2] += (uint64_t)(h - nd) * (uint64_t)slots[s].P.m * slots[s].n_att;
 }
 
 __global__ void k_flat_batch(const BatchSlot* __restrict__ slots, int max_h) {
@@ -915,11 +1009,16 @@ __global__ void k_flat_batch(const BatchSlot* __restrict__ slots, int max_h) {
   flat_merge_body(P, S, a);
 }
 
-// Copies every slot's count of finished windows into one array (-1 for a free slot).
-__global__ void k_gather_done(const BatchSlot* __restrict__ slots, int n_slots, int32_t* out) {
+// Copies every slot's count of finished windows and its clocks into one array.
+__global__ void k_slot_report(const BatchSlot* __restrict__ slots, int n_slots, SlotReport* out) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n_slots) return;
-  out[s] = slots[s].active ? *slots[s].S.n_done : -1;
+  SlotReport r{-1, 0, 0, 0, 0};
+  if (slots[s].active) {
+    const uint64_t* clk = slots[s].S.clock;
+    r = SlotReport{*slots[s].S.n_done, 1, clk[0], clk[1], clk[2]};
+  }
+  out[s] = r;
 }
 
 // k_sweep_batch has a few bytes of static shared memory, so its dynamic
@@ -927,19 +1026,12 @@ __global__ void k_gather_done(const BatchSlot* __restrict__ slots, int n_slots, 
 constexpr int kBatchDynSmem = 226 * 1024;
 
 cudaError_t prepare_sweep_batch() {
-  cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<kIsing>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_sweep_batch<kPotts>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_sweep_batch<kEA>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  return cudaFuncSetAttribute(k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
 }
 
-cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, BatchWalker* const d_lists[3],
-                               const int n_list[3], const size_t smem[3], int max_pairs, int max_m, int max_h,
-                               cudaStream_t st) {
-  if (n_list[kIsing] > 0) k_sweep_batch<kIsing><<<n_list[kIsing], 32, smem[kIsing], st>>>(d_slots, d_lists[kIsing]);
-  if (n_list[kPotts] > 0) k_sweep_batch<kPotts><<<n_list[kPotts], 32, smem[kPotts], st>>>(d_slots, d_lists[kPotts]);
-  if (n_list[kEA] > 0) k_sweep_batch<kEA><<<n_list[kEA], 32, smem[kEA], st>>>(d_slots, d_lists[kEA]);
+cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, const BatchWalker* d_list, int n_list,
+                               size_t smem, int max_pairs, int max_m, int max_h, cudaStream_t st) {
+  if (n_list > 0) k_sweep_batch<<<n_list, 32, smem, st>>>(d_slots, d_list);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (max_pairs > 0) {
@@ -951,8 +1043,9 @@ cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, BatchWalke
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_done(const BatchSlot* d_slots, int n_slots, int32_t* out, cudaStream_t st) {
-  k_gather_done<<<(n_slots + 127) / 128, 128, 0, st>>>(d_slots, n_slots, out);
+cudaError_t launch_slot_report(const BatchSlot* d_slots, int n_slots, SlotReport* out, cudaStream_t st) {
+  if (n_slots <= 0) return cudaSuccess;
+  k_slot_report<<<(n_slots + 127) / 128, 128, 0, st>>>(d_slots, n_slots, out);
   return cudaGetLastError();
 }
 

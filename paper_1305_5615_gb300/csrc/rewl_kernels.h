@@ -13,6 +13,8 @@ size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant);
 cudaError_t prepare_sweep(int G, int model);
 cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const SweepLaunch& A, cudaStream_t st);
 cudaError_t launch_exchange(const Problem& P, const DevState& S, cudaStream_t st);
+cudaError_t launch_precompute(int G, const Problem& P, uint64_t t0, uint32_t n_att, uint32_t stride, PreTrial* out,
+                              cudaStream_t st);
 cudaError_t launch_advance_clock(const DevState& S, uint32_t sweeps, cudaStream_t st);
 cudaError_t launch_flat_merge(const Problem& P, const DevState& S, cudaStream_t st);
 cudaError_t launch_init(const Problem& P, const DevState& S, cudaStream_t st);
@@ -21,9 +23,8 @@ cudaError_t launch_entry(const Problem& P, const DevState& S, uint64_t budget, c
 
 // served form (rewl_server.cu)
 cudaError_t prepare_sweep_batch();
-cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, BatchWalker* const d_lists[3],
-                               const int n_list[3], const size_t smem[3], int max_pairs, int max_m, int max_h,
-                               cudaStream_t st);
-cudaError_t launch_gather_done(const BatchSlot* d_slots, int n_slots, int32_t* out, cudaStream_t st);
+cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, const BatchWalker* d_list, int n_list,
+                               size_t smem, int max_pairs, int max_m, int max_h, cudaStream_t st);
+cudaError_t launch_slot_report(const BatchSlot* d_slots, int n_slots, SlotReport* out, cudaStream_t st);
 
 }  // namespace rewl

@@ -6,7 +6,7 @@
 //   lng   f64 [n_walkers][w]           ln g over the window's w bins
 //   H     u32 [n_walkers][w]           visit histogram of the iteration
 //   J     u32 [2][L][Wr1]              +-J couplings, bit 1 = J -1 (planes: right, down)
-//   win_start i32 [h], lnf f64 [h], iter i32 [h], done i32 [h]
+//   win_start i32 [h], lnf f64 [h], iter i32 [h], done i32 [h], stage i32 [h]
 //   counters u64: wl_accept / near_ties / exact_tests [n_walkers], x_tried / x_accepted [h]
 #pragma once
 #include <cstdint>
@@ -26,6 +26,7 @@ struct Problem {
   int h, m, w, n_walkers;
   uint32_t magic_L;  // ceil(2^32 / L): y = mulhi(site, magic_L) for site < N
   uint32_t seed_lo, seed_hi;
+  int wl_rule;     // 0: flatness rule; 1: 1/t rule
   double flatness, lnf_final;
 };
 
@@ -49,7 +50,8 @@ struct DevState {
   int32_t* status;       // per walker: 0 ok, else a rewl_status
   uint64_t* entry_t;     // per walker counter of the entry stream
   uint32_t* seed_config; // restart configuration for the entry walk
-  uint64_t* clock;       // [0] sweeps done by the solve, [1] exchange rounds done
+  uint64_t* clock;       // [0] sweeps done by the solve, [1] exchange rounds done, [2] trials (batched rounds)
+  int32_t* stage;        // [h] 1/t rule: 0 = halving on the histogram test, 1 = following 1/t
 };
 
 // Sweep kernel variants (identical results): the staged form keeps H in
@@ -57,12 +59,23 @@ struct DevState {
 // speculates two deep and rebuilds H from the shadow.
 enum SweepVariant : int { kSweepChain = 0, kSweepStaged = 1 };
 
+// A trial's draw, prepared ahead of its sweep launch by k_precompute: the
+// site (x | y << 8), the proposed Potts offset (<< 16), the mask of earlier
+// trials of its group that touch its neighbourhood, and ln u in 2^-40 units.
+struct PreTrial {
+  uint32_t pk;
+  uint32_t mask;
+  int64_t thr;
+};
+
 struct SweepLaunch {
   uint32_t n_att;     // trials per walker in this launch (sweeps * N); the first
                       // trial's index is clock[0] * N, read on the device
   int n_active;       // walkers in `active`
   int wpb;            // walkers per CTA
   int variant;        // SweepVariant
+  const PreTrial* pre;  // prepared draws [walker][pre_stride] or nullptr (drawn in the kernel)
+  uint32_t pre_stride;
 };
 
 // One request slot of the served form: the request's sizes and device
@@ -78,6 +91,14 @@ struct BatchSlot {
 struct BatchWalker {
   int slot;
   int W;
+};
+// What the host reads of a slot after a round: finished windows and the clocks.
+struct SlotReport {
+  int32_t n_done;     // -1 for a free slot
+  int32_t active;
+  uint64_t sweeps;    // clock[0]
+  uint64_t rounds;    // clock[1]
+  uint64_t attempts;  // clock[2]: WL trials of all walkers (counted by the batched rounds)
 };
 
 }  // namespace rewl

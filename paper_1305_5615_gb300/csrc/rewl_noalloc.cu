@@ -160,7 +160,7 @@ extern "C" rewl_status rewl_sweep_noalloc(const rewl_sweep_desc* d, uint32_t* la
     return REWL_ECUDA;
   }
   if (d->sweeps == 0) return REWL_OK;
-  SweepLaunch A;
+  SweepLaunch A{};
   A.n_att = (uint32_t)(d->sweeps * P.N);
   A.n_active = (int)n_walkers;
   A.wpb = wpb;

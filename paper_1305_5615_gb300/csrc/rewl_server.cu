@@ -1,12 +1,19 @@
 // rewl_server.cu -- the served form of REWL: density-of-states requests of
 // different models and lattice sizes arrive at any time, are admitted while
-// request slots and the device-memory budget allow, and run together.  Each
-// round is one launch per model of the sweep kernel over every walker of every
-// running request, one batched exchange launch, one clock launch and one
-// batched flatness launch; requests that finish are retired (their joined
-// ln g is read back) and their memory goes to the queue.  Every request keeps
-// its own seed, schedule and state, so its result is bit-identical to the one
-// it gets alone (rewl_create + rewl_step).
+// request slots and the device-memory budget allow, and run together.
+//
+// Running requests are grouped by shape (model, L): the walkers of one group
+// all take about the same time per block, so a group advances in rounds --
+// one fused sweep launch over every walker of every request of the group,
+// then one launch each for the exchanges, the clocks and the due flatness
+// checks of all its requests, and a small report read back.  Each group has
+// a CUDA stream of its own and its rounds are issued as soon as the previous
+// one has been read, so groups of different sizes run side by side on the
+// GPU at their own pace (a 12 x 12 glass is not held back by a 32 x 32 Potts
+// lattice).  Requests that finish are retired when their group's round has
+// been read: their joined ln g is read back and their memory goes to the
+// queue.  Every request keeps its own seed, schedule and state, so its result
+// is bit-identical to the one it gets alone (rewl_create + rewl_step).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,7 +23,9 @@
 #include <cstdio>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -60,7 +69,7 @@ struct Request {
   int64_t bytes = 0;
   Clock::time_point t_submit, t_admit, t_done;
   rewl_ctx* ctx = nullptr;
-  int slot = -1;
+  int group = -1, slot = -1;
   int n_done = 0;
   int64_t sweeps = 0, attempts = 0;
   std::vector<double> lng;
@@ -83,40 +92,40 @@ int64_t request_bytes(const Request& r) {
          2LL * L * Wr1 * 4 + 4096;
 }
 
-}  // namespace
-
-struct rewl_server {
-  std::mutex mu;
-  rewl_params params{};
-  int64_t budget = 0, in_use = 0;
-  int max_running = 0;
+// Running requests of one shape (model, L) and the device tables of their rounds.
+// `slots` is the host copy of the slot table; it is staged through pinned memory
+// and uploaded only when a round is issued, i.e. while no round of the group is
+// in flight, so the staging buffers are never rewritten under a pending copy.
+struct Group {
+  int model = 0, L = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  uint64_t next_id = 1;
-  std::deque<uint64_t> queue;
-  std::unordered_map<uint64_t, Request> reqs;
-  std::vector<uint64_t> slot_req;  // request id per slot, 0 = free
-  std::vector<BatchSlot> h_slots;
-  BatchSlot* d_slots = nullptr;
-  BatchWalker* d_lists[3] = {nullptr, nullptr, nullptr};
-  int list_cap[3] = {0, 0, 0};
-  int n_list[3] = {0, 0, 0};
-  size_t smem[3] = {0, 0, 0};
+  cudaEvent_t ev = nullptr;
+  bool in_flight = false;
+  std::vector<uint64_t> slot_req;   // request id per slot, 0 = free
+  std::vector<uint64_t> launched;   // request id per slot in the round in flight
+  std::vector<BatchSlot> slots;     // slot table
+  int cap = 0;                      // slots the device tables hold
+  BatchSlot* h_stage = nullptr;     // pinned [cap]
+  BatchSlot* d_slots = nullptr;     // [cap]
+  SlotReport* h_rep = nullptr;      // pinned [cap]
+  SlotReport* d_rep = nullptr;      // [cap]
+  BatchWalker* h_list = nullptr;    // pinned [list_cap]
+  BatchWalker* d_list = nullptr;    // [list_cap]
+  int list_cap = 0, n_list = 0, hi = 0;  // hi: slots [0, hi) in the round
+  size_t smem = 0;
   int max_pairs = 0, max_m = 1, max_h = 1;
-  bool lists_dirty = true;
-  int32_t* d_done = nullptr;
-  int32_t* h_done = nullptr;  // pinned
-  int64_t rounds = 0, attempts = 0;
-  int finished = 0, failed = 0;
+  bool dirty = true;
 
-  ~rewl_server() {
+  ~Group() {
     if (stream) cudaStreamSynchronize(stream);
-    for (auto& kv : reqs)
-      if (kv.second.ctx) rewl_destroy(kv.second.ctx);
     cudaFree(d_slots);
-    for (int k = 0; k < 3; ++k) cudaFree(d_lists[k]);
-    cudaFree(d_done);
-    if (h_done) cudaFreeHost(h_done);
+    cudaFree(d_rep);
+    cudaFree(d_list);
+    if (h_stage) cudaFreeHost(h_stage);
+    if (h_rep) cudaFreeHost(h_rep);
+    if (h_list) cudaFreeHost(h_list);
+    if (ev) cudaEventDestroy(ev);
     if (own_stream && stream) cudaStreamDestroy(stream);
   }
 
@@ -125,10 +134,63 @@ struct rewl_server {
     for (uint64_t id : slot_req) n += id != 0;
     return n;
   }
+};
 
-  rewl_status upload_slot(int s) {
-    SCUDA(cudaMemcpyAsync(d_slots + s, &h_slots[s], sizeof(BatchSlot), cudaMemcpyHostToDevice, stream));
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+struct rewl_server {
+  std::mutex mu;
+  rewl_params params{};
+  int64_t budget = 0, in_use = 0;
+  int max_running = 0, n_running = 0;
+  uint64_t next_id = 1;
+  std::deque<uint64_t> queue;
+  std::unordered_map<uint64_t, Request> reqs;
+  std::vector<std::unique_ptr<Group>> groups;
+  int64_t rounds = 0, attempts = 0;
+  int finished = 0, failed = 0;
+
+  ~rewl_server() {
+    for (auto& g : groups)
+      if (g->stream) cudaStreamSynchronize(g->stream);
+    for (auto& kv : reqs)
+      if (kv.second.ctx) rewl_destroy(kv.second.ctx);
+    groups.clear();
+  }
+
+  rewl_status group_for(int model, int L, int* out) {
+    for (size_t i = 0; i < groups.size(); ++i)
+      if (groups[i]->model == model && groups[i]->L == L) {
+        *out = (int)i;
+        return REWL_OK;
+      }
+    auto g = std::make_unique<Group>();
+    g->model = model;
+    g->L = L;
+    if (params.stream) {
+      g->stream = (cudaStream_t)params.stream;
+    } else {
+      SCUDA(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+      g->own_stream = true;
+    }
+    SCUDA(cudaEventCreateWithFlags(&g->ev, cudaEventDisableTiming));
+    groups.push_back(std::move(g));
+    *out = (int)groups.size() - 1;
     return REWL_OK;
+  }
+
+  // A free slot of group g (host tables only; the device tables follow at the next round).
+  int take_slot(Group& g) {
+    for (size_t i = 0; i < g.slot_req.size(); ++i)
+      if (!g.slot_req[i]) return (int)i;
+    g.slot_req.push_back(0);
+    g.launched.push_back(0);
+    g.slots.push_back(BatchSlot{});
+    return (int)g.slot_req.size() - 1;
   }
 
   // Admission: first-come first-served while a slot and the memory budget allow.
@@ -136,20 +198,15 @@ struct rewl_server {
     while (!queue.empty()) {
       const uint64_t id = queue.front();
       Request& r = reqs[id];
-      int s = -1;
-      for (int i = 0; i < max_running; ++i)
-        if (!slot_req[i]) {
-          s = i;
-          break;
-        }
-      if (s < 0 || in_use + r.bytes > budget) break;  // head of queue waits for capacity
+      if (n_running >= max_running || in_use + r.bytes > budget) break;  // head of queue waits
       queue.pop_front();
       rewl_params p = params;
-      p.stream = (void*)stream;
+      p.stream = params.stream;  // NULL: the request gets a stream of its own for its set-up
       p.lanes_per_walker = 32;
       p.walkers_per_block = 1;
       p.mode = REWL_MODE_PLAIN;
       p.profile = 0;
+      p.prefetch_draws = -1;  // the batched kernels draw in-kernel
       rewl_handle h = nullptr;
       const rewl_status st = rewl_create(&h, &r.model, &r.lattice, r.has_couplings ? r.couplings.data() : nullptr,
                                          r.windows, r.overlap, r.walkers_per_window, r.flatness, r.lnf_final, r.seed,
@@ -161,67 +218,129 @@ struct rewl_server {
         ++failed;
         continue;
       }
+      int gi = -1;
+      const rewl_status gs = group_for(r.model.kind, r.lattice.Lx, &gi);
+      if (gs != REWL_OK) {
+        rewl_destroy(h);
+        return gs;
+      }
+      Group& g = *groups[gi];
+      const int s = take_slot(g);
       r.ctx = h;
+      r.group = gi;
       r.slot = s;
       r.state = REWL_REQ_RUNNING;
       r.t_admit = Clock::now();
       in_use += r.bytes;
-      slot_req[s] = id;
-      BatchSlot& b = h_slots[s];
+      ++n_running;
+      g.slot_req[s] = id;
+      BatchSlot& b = g.slots[s];
       b.P = h->P;
       b.S = h->S;
       b.spe = (uint32_t)h->params.sweeps_per_exchange;
       b.spf = (uint32_t)h->params.sweeps_per_flat_check;
       b.n_att = b.spe * (uint32_t)h->P.N;
       b.active = 1;
-      rewl_status us = upload_slot(s);
-      if (us != REWL_OK) return us;
-      lists_dirty = true;
+      g.dirty = true;
     }
     return REWL_OK;
   }
 
-  rewl_status rebuild_lists() {
-    std::vector<BatchWalker> L[3];
-    max_pairs = 0;
-    max_m = 1;
-    max_h = 1;
-    for (int k = 0; k < 3; ++k) smem[k] = 0;
-    for (int s = 0; s < max_running; ++s) {
-      if (!slot_req[s]) continue;
-      const Problem& P = h_slots[s].P;
-      for (int W = 0; W < P.n_walkers; ++W) L[P.model].push_back(BatchWalker{s, W});
-      smem[P.model] = std::max(smem[P.model], sweep_smem_bytes(P, 1, 32, kSweepChain));
-      max_pairs = std::max(max_pairs, P.h / 2);
-      max_m = std::max(max_m, P.m);
-      max_h = std::max(max_h, P.h);
-    }
-    for (int k = 0; k < 3; ++k) {
-      n_list[k] = (int)L[k].size();
-      if (n_list[k] > list_cap[k]) {
-        cudaFree(d_lists[k]);
-        d_lists[k] = nullptr;
-        const int cap = std::max(n_list[k], 2 * list_cap[k]);
-        if (cudaMalloc(&d_lists[k], sizeof(BatchWalker) * cap) != cudaSuccess) {
-          list_cap[k] = 0;
-          return sfail(REWL_ENOMEM, "walker list of %d entries", cap);
-        }
-        list_cap[k] = cap;
+  // Uploads the group's slot table and walker list (before a launch, nothing in flight).
+  rewl_status rebuild(Group& g) {
+    const int need = (int)g.slots.size();
+    if (need > g.cap) {
+      const int cap = std::max(need, 2 * g.cap);
+      BatchSlot *hs = nullptr, *ds = nullptr;
+      SlotReport *hr = nullptr, *dr = nullptr;
+      if (cudaMallocHost(&hs, sizeof(BatchSlot) * cap) != cudaSuccess ||
+          cudaMallocHost(&hr, sizeof(SlotReport) * cap) != cudaSuccess ||
+          cudaMalloc(&ds, sizeof(BatchSlot) * cap) != cudaSuccess ||
+          cudaMalloc(&dr, sizeof(SlotReport) * cap) != cudaSuccess) {
+        if (hs) cudaFreeHost(hs);
+        if (hr) cudaFreeHost(hr);
+        cudaFree(ds);
+        cudaFree(dr);
+        return sfail(REWL_ENOMEM, "group tables of %d slots", cap);
       }
-      if (n_list[k])
-        SCUDA(cudaMemcpyAsync(d_lists[k], L[k].data(), sizeof(BatchWalker) * n_list[k], cudaMemcpyHostToDevice, stream));
+      if (g.h_stage) cudaFreeHost(g.h_stage);
+      if (g.h_rep) cudaFreeHost(g.h_rep);
+      cudaFree(g.d_slots);
+      cudaFree(g.d_rep);
+      g.h_stage = hs;
+      g.h_rep = hr;
+      g.d_slots = ds;
+      g.d_rep = dr;
+      g.cap = cap;
     }
-    lists_dirty = false;
+    int n = 0, hi = 0;
+    g.max_pairs = 0;
+    g.max_m = 1;
+    g.max_h = 1;
+    g.smem = 0;
+    for (int s = 0; s < need; ++s) {
+      g.h_stage[s] = g.slots[s];
+      if (!g.slot_req[s]) continue;
+      const Problem& P = g.slots[s].P;
+      n += P.n_walkers;
+      hi = s + 1;
+      g.smem = std::max(g.smem, sweep_smem_bytes(P, 1, 32, kSweepChain));
+      g.max_pairs = std::max(g.max_pairs, P.h / 2);
+      g.max_m = std::max(g.max_m, P.m);
+      g.max_h = std::max(g.max_h, P.h);
+    }
+    g.hi = hi;
+    if (n > g.list_cap) {
+      const int cap = std::max(n, 2 * g.list_cap);
+      BatchWalker *hl = nullptr, *dl = nullptr;
+      if (cudaMallocHost(&hl, sizeof(BatchWalker) * cap) != cudaSuccess ||
+          cudaMalloc(&dl, sizeof(BatchWalker) * cap) != cudaSuccess) {
+        if (hl) cudaFreeHost(hl);
+        cudaFree(dl);
+        return sfail(REWL_ENOMEM, "walker list of %d entries", cap);
+      }
+      if (g.h_list) cudaFreeHost(g.h_list);
+      cudaFree(g.d_list);
+      g.h_list = hl;
+      g.d_list = dl;
+      g.list_cap = cap;
+    }
+    int k = 0;
+    for (int s = 0; s < hi; ++s) {
+      if (!g.slot_req[s]) continue;
+      for (int W = 0; W < g.slots[s].P.n_walkers; ++W) g.h_list[k++] = BatchWalker{s, W};
+    }
+    g.n_list = n;
+    if (hi) SCUDA(cudaMemcpyAsync(g.d_slots, g.h_stage, sizeof(BatchSlot) * hi, cudaMemcpyHostToDevice, g.stream));
+    if (n) SCUDA(cudaMemcpyAsync(g.d_list, g.h_list, sizeof(BatchWalker) * n, cudaMemcpyHostToDevice, g.stream));
+    g.dirty = false;
+    return REWL_OK;
+  }
+
+  // One round of group g: sweeps, exchanges, clocks, due flatness checks, report.
+  rewl_status launch(Group& g) {
+    if (g.dirty) {
+      rewl_status st = rebuild(g);
+      if (st != REWL_OK) return st;
+    }
+    if (g.n_list == 0) return REWL_OK;
+    SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list, g.n_list, g.smem, g.max_pairs, g.max_m, g.max_h, g.stream));
+    SCUDA(launch_slot_report(g.d_slots, g.hi, g.d_rep, g.stream));
+    SCUDA(cudaMemcpyAsync(g.h_rep, g.d_rep, sizeof(SlotReport) * g.hi, cudaMemcpyDeviceToHost, g.stream));
+    SCUDA(cudaEventRecord(g.ev, g.stream));
+    for (int i = 0; i < (int)g.slot_req.size(); ++i) g.launched[i] = i < g.hi ? g.slot_req[i] : 0;
+    g.in_flight = true;
     return REWL_OK;
   }
 
   void release(Request& r) {
-    if (r.slot >= 0) {
-      h_slots[r.slot].active = 0;
-      upload_slot(r.slot);
-      slot_req[r.slot] = 0;
-      r.slot = -1;
-      lists_dirty = true;
+    if (r.group >= 0) {
+      Group& g = *groups[r.group];
+      g.slots[r.slot].active = 0;
+      g.slot_req[r.slot] = 0;
+      g.dirty = true;
+      r.group = r.slot = -1;
+      --n_running;
     }
     if (r.ctx) {
       rewl_destroy(r.ctx);
@@ -230,36 +349,23 @@ struct rewl_server {
     }
   }
 
-  rewl_status round() {
-    if (lists_dirty) {
-      rewl_status st = rebuild_lists();
-      if (st != REWL_OK) return st;
-    }
-    // walkers of windows still running: what this round's sweeps count
-    for (int s = 0; s < max_running; ++s) {
-      if (!slot_req[s]) continue;
-      Request& r = reqs[slot_req[s]];
-      const Problem& P = h_slots[s].P;
-      const int64_t n = (int64_t)(P.h - r.n_done) * P.m * h_slots[s].spe * P.N;
-      r.attempts += n;
-      attempts += n;
-      r.sweeps += h_slots[s].spe;
-      r.ctx->attempts += (uint64_t)n;
-      r.ctx->sweep_clock += h_slots[s].spe;
-      r.ctx->xround += 1;
-    }
-    SCUDA(launch_round_batch(d_slots, max_running, d_lists, n_list, smem, max_pairs, max_m, max_h, stream));
-    SCUDA(launch_gather_done(d_slots, max_running, d_done, stream));
-    SCUDA(cudaMemcpyAsync(h_done, d_done, sizeof(int32_t) * max_running, cudaMemcpyDeviceToHost, stream));
-    SCUDA(cudaStreamSynchronize(stream));
+  // Reads the report of a finished round of g; retires requests whose windows are all done.
+  void collect(Group& g) {
+    g.in_flight = false;
     ++rounds;
-    for (int s = 0; s < max_running; ++s) {
-      if (!slot_req[s]) continue;
-      Request& r = reqs[slot_req[s]];
-      r.n_done = h_done[s];
-      r.ctx->n_done = h_done[s];
-      if (h_done[s] < h_slots[s].P.h) continue;
-      // finished: read the joined ln g back, then free the slot and memory
+    for (int s = 0; s < g.hi; ++s) {
+      if (!g.slot_req[s] || g.launched[s] != g.slot_req[s]) continue;  // not in that round
+      Request& r = reqs[g.slot_req[s]];
+      const SlotReport& q = g.h_rep[s];
+      attempts += (int64_t)q.attempts - r.attempts;
+      r.attempts = (int64_t)q.attempts;
+      r.sweeps = (int64_t)q.sweeps;
+      r.n_done = q.n_done;
+      r.ctx->sweep_clock = q.sweeps;
+      r.ctx->xround = q.rounds;
+      r.ctx->attempts = q.attempts;
+      r.ctx->n_done = q.n_done;
+      if (q.n_done < g.slots[s].P.h) continue;
       r.lng.assign(r.ctx->P.n_bins, 0.0);
       const rewl_status st = rewl_get_lng(r.ctx, r.lng.data(), (int32_t)r.lng.size(), &r.n_bins, &r.e_min, &r.e_step);
       r.t_done = Clock::now();
@@ -273,13 +379,42 @@ struct rewl_server {
       }
       release(r);
     }
-    return REWL_OK;
+  }
+
+  // Issues a round for every idle group with running requests, then waits until
+  // at least one round in flight has finished and collects every finished one.
+  rewl_status step() {
+    int n_flight = 0;
+    for (auto& gp : groups) {
+      Group& g = *gp;
+      if (!g.in_flight && g.running() > 0) {
+        rewl_status st = launch(g);
+        if (st != REWL_OK) return st;
+      }
+      n_flight += g.in_flight;
+    }
+    if (!n_flight) return REWL_OK;
+    const Clock::time_point t0 = Clock::now();
+    for (long spin = 0;; ++spin) {
+      int got = 0;
+      for (auto& gp : groups) {
+        Group& g = *gp;
+        if (!g.in_flight) continue;
+        const cudaError_t e = cudaEventQuery(g.ev);
+        if (e == cudaErrorNotReady) continue;
+        if (e != cudaSuccess) return sfail(REWL_ECUDA, "round: %s", cudaGetErrorString(e));
+        collect(g);
+        ++got;
+      }
+      if (got) return REWL_OK;
+      if (spin > 64) {
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+        if (params.timeout_ms > 0 && ms_between(t0, Clock::now()) > (double)params.timeout_ms)
+          return sfail(REWL_ETIMEOUT, "no round finished within %lld ms", (long long)params.timeout_ms);
+      }
+    }
   }
 };
-
-static double ms_between(Clock::time_point a, Clock::time_point b) {
-  return std::chrono::duration<double, std::milli>(b - a).count();
-}
 
 extern "C" {
 
@@ -293,27 +428,11 @@ rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, in
   else rewl_params_default(&s->params);
   s->budget = device_bytes;
   s->max_running = max_running;
-  s->slot_req.assign(max_running, 0);
-  s->h_slots.assign(max_running, BatchSlot{});
-  auto bail = [&](rewl_status st) {
+  const cudaError_t e = prepare_sweep_batch();
+  if (e != cudaSuccess) {
     delete s;
-    return st;
-  };
-  if (s->params.stream) {
-    s->stream = (cudaStream_t)s->params.stream;
-  } else {
-    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
-      return bail(sfail(REWL_ECUDA, "cudaStreamCreate failed"));
-    s->own_stream = true;
+    return sfail(REWL_ECUDA, "server set-up: %s", cudaGetErrorString(e));
   }
-  if (cudaMalloc(&s->d_slots, sizeof(BatchSlot) * max_running) != cudaSuccess ||
-      cudaMalloc(&s->d_done, sizeof(int32_t) * max_running) != cudaSuccess ||
-      cudaMallocHost(&s->h_done, sizeof(int32_t) * max_running) != cudaSuccess)
-    return bail(sfail(REWL_ENOMEM, "server tables"));
-  cudaError_t e = cudaMemsetAsync(s->d_slots, 0, sizeof(BatchSlot) * max_running, s->stream);
-  if (e == cudaSuccess) e = prepare_sweep_batch();
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return bail(sfail(REWL_ECUDA, "server set-up: %s", cudaGetErrorString(e)));
   *out = s;
   return REWL_OK;
 }
@@ -356,14 +475,14 @@ rewl_status rewl_server_run(rewl_server_handle s, int32_t max_rounds, rewl_serve
   for (int32_t k = 0; k < max_rounds; ++k) {
     rewl_status st = s->admit();
     if (st != REWL_OK) return st;
-    if (s->running() == 0) break;
-    st = s->round();
+    if (s->n_running == 0) break;
+    st = s->step();
     if (st != REWL_OK) return st;
   }
-  rewl_status st = s->admit();  // fill slots freed by the last round
+  rewl_status st = s->admit();  // fill slots freed by the last rounds
   if (st != REWL_OK) return st;
   if (stats) {
-    stats->running = s->running();
+    stats->running = s->n_running;
     stats->queued = (int32_t)s->queue.size();
     stats->finished = s->finished;
     stats->failed = s->failed;
@@ -419,7 +538,10 @@ rewl_status rewl_server_cancel(rewl_server_handle s, uint64_t id) {
   if (r.state == REWL_REQ_QUEUED) {
     s->queue.erase(std::remove(s->queue.begin(), s->queue.end(), id), s->queue.end());
   } else if (r.state == REWL_REQ_RUNNING) {
-    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return sfail(REWL_ECUDA, "synchronise");
+    Group& g = *s->groups[r.group];
+    if (cudaStreamSynchronize(g.stream) != cudaSuccess) return sfail(REWL_ECUDA, "synchronise");
+    if (g.in_flight) s->collect(g);  // the round it was part of; the request may finish in it
+    if (r.state != REWL_REQ_RUNNING) return REWL_OK;
     s->release(r);
   } else {
     return REWL_OK;  // already finished

@@ -17,6 +17,8 @@ from . import _build
 ISING, POTTS, EA_PM_J = 0, 1, 2
 MODE_PLAIN, MODE_GRAPH = 0, 1
 MODELS = {"ising": ISING, "potts": POTTS, "ea": EA_PM_J, "pmj": EA_PM_J}
+RULE_FLAT, RULE_ONE_OVER_T = 0, 1
+WL_RULES = {"flat": RULE_FLAT, "1/t": RULE_ONE_OVER_T}
 
 STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: "REWL_ETIMEOUT", 5: "REWL_EENTRY",
           6: "REWL_EOVERFLOW", 7: "REWL_EBUSY", 8: "REWL_ENOTFOUND", 9: "REWL_ENODEV"}
@@ -24,7 +26,8 @@ STATUS = {0: "REWL_OK", 1: "REWL_EINVAL", 2: "REWL_ENOMEM", 3: "REWL_ECUDA", 4: 
 EXPORTED = ["rewl_params_default", "rewl_create", "rewl_step", "rewl_get_lng", "rewl_get_window_lng",
             "rewl_get_info", "rewl_get_state", "rewl_set_state", "rewl_destroy", "rewl_status_str",
             "rewl_last_error", "rewl_sweep_noalloc", "rewl_server_create", "rewl_server_submit", "rewl_server_run",
-            "rewl_server_poll", "rewl_server_result", "rewl_server_cancel", "rewl_server_destroy"]
+            "rewl_server_poll", "rewl_server_result", "rewl_server_cancel", "rewl_server_destroy", "rewl_thermo",
+            "rewl_thermo_jackknife"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 
@@ -52,7 +55,7 @@ class rewl_params(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int64), ("stream", ctypes.c_void_p), ("lanes_per_walker", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("mode", ctypes.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("profile", ctypes.c_int32),
-                ("sweep_variant", ctypes.c_int32)]
+                ("sweep_variant", ctypes.c_int32), ("prefetch_draws", ctypes.c_int32), ("wl_rule", ctypes.c_int32)]
 
 
 class rewl_info(ctypes.Structure):
@@ -61,7 +64,7 @@ class rewl_info(ctypes.Structure):
                  "e_step", "lattice_words", "lanes_per_walker", "walkers_per_block", "mode", "windows_done")] + \
                [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
-                ("d2h_bytes", ctypes.c_int64)]
+                ("d2h_bytes", ctypes.c_int64), ("prefetch_draws", ctypes.c_int32)]
 
 
 class rewl_sweep_desc(ctypes.Structure):
@@ -93,7 +96,7 @@ class rewl_state(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in
                 ("lattice", "E", "lng", "H", "win_start", "lnf", "iteration", "done", "wl_accept", "near_ties",
                  "exact_tests", "x_tried", "x_accepted")] + \
-               [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64)]
+               [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("stage", ctypes.c_void_p)]
 
 
 _lib = None
@@ -157,6 +160,11 @@ def load(build_if_missing=True):
     L.rewl_server_cancel.restype = ctypes.c_int
     L.rewl_server_destroy.argtypes = [P]
     L.rewl_server_destroy.restype = None
+    L.rewl_thermo.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, ctypes.c_int32, P]
+    L.rewl_thermo_jackknife.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
+                                        ctypes.c_int32, P, P]
+    L.rewl_thermo_jackknife.restype = ctypes.c_int
+    L.rewl_thermo.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -224,7 +232,7 @@ def rewl_get_state(h, info):
          "win_start": np.zeros(hw, np.int32), "lnf": np.zeros(hw, np.float64), "iteration": np.zeros(hw, np.int32),
          "done": np.zeros(hw, np.int32), "wl_accept": np.zeros(nW, np.uint64), "near_ties": np.zeros(nW, np.uint64),
          "exact_tests": np.zeros(nW, np.uint64), "x_tried": np.zeros(hw, np.uint64),
-         "x_accepted": np.zeros(hw, np.uint64)}
+         "x_accepted": np.zeros(hw, np.uint64), "stage": np.zeros(hw, np.int32)}
     s = rewl_state(**{k: _p(v) for k, v in a.items()})
     _check(load().rewl_get_state(h, ctypes.byref(s)), "rewl_get_state")
     a["sweep_clock"], a["exchange_rounds"] = s.sweep_clock, s.exchange_rounds
@@ -248,6 +256,27 @@ def rewl_sweep_noalloc(desc, lattice, E, lng, H, coupling_bits, win_start, lnf, 
     torch tensor .data_ptr()); the library allocates nothing for this call."""
     ptrs = [ctypes.c_void_p(p) if p else None for p in (lattice, E, lng, H, coupling_bits, win_start, lnf, stream)]
     _check(load().rewl_sweep_noalloc(ctypes.byref(desc), *ptrs), "rewl_sweep_noalloc")
+
+
+def rewl_thermo(lng, e_min, e_step, temperatures):
+    """Canonical ln Z, U, C, F, S (columns) at each temperature, from ln g."""
+    g = np.ascontiguousarray(lng, dtype=np.float64)
+    T = np.ascontiguousarray(temperatures, dtype=np.float64)
+    out = np.zeros((len(T), 5), np.float64)
+    _check(load().rewl_thermo(_p(g), len(g), e_min, e_step, _p(T), len(T), _p(out)), "rewl_thermo")
+    return out
+
+
+def rewl_thermo_jackknife(lng_runs, e_min, e_step, temperatures):
+    """rewl_thermo's quantities of the mean ln g over runs, with jackknife
+    errors over the runs: (estimate, error), each [n_T][5]."""
+    g = np.ascontiguousarray(lng_runs, dtype=np.float64)
+    T = np.ascontiguousarray(temperatures, dtype=np.float64)
+    est = np.zeros((len(T), 5), np.float64)
+    err = np.zeros((len(T), 5), np.float64)
+    _check(load().rewl_thermo_jackknife(_p(g), g.shape[0], g.shape[1], e_min, e_step, _p(T), len(T), _p(est), _p(err)),
+           "rewl_thermo_jackknife")
+    return est, err
 
 
 def rewl_status_str(status):
@@ -281,7 +310,7 @@ class REWL:
                  couplings=None, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
                  entry_max_sweeps=1000, discovery_sweeps=200, timeout_ms=0, lanes_per_walker=0,
                  walkers_per_block=0, mode=MODE_PLAIN, stream=None, torch_allocator=False, profile=False,
-                 sweep_variant=0):
+                 sweep_variant=0, prefetch_draws=0, wl_rule=0):
         if isinstance(model, str):
             model = MODELS[model]
         p = rewl_params_default()
@@ -290,6 +319,8 @@ class REWL:
         p.lanes_per_walker, p.walkers_per_block, p.mode = lanes_per_walker, walkers_per_block, mode
         p.profile = 1 if profile else 0
         p.sweep_variant = sweep_variant
+        p.prefetch_draws = prefetch_draws
+        p.wl_rule = WL_RULES[wl_rule] if isinstance(wl_rule, str) else wl_rule
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._keep = None
@@ -337,11 +368,13 @@ class RewlServer:
     run together (rewl_server_* of include/rewl.h)."""
 
     def __init__(self, device_bytes, max_running, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
-                 entry_max_sweeps=1000, discovery_sweeps=200, stream=None):
+                 entry_max_sweeps=1000, discovery_sweeps=200, stream=None, wl_rule=0, timeout_ms=0):
         L = load()
         p = rewl_params_default()
         p.sweeps_per_exchange, p.sweeps_per_flat_check, p.lnf0 = sweeps_per_exchange, sweeps_per_flat_check, lnf0
         p.entry_max_sweeps, p.discovery_sweeps = entry_max_sweeps, discovery_sweeps
+        p.wl_rule = WL_RULES[wl_rule] if isinstance(wl_rule, str) else wl_rule
+        p.timeout_ms = timeout_ms
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._h = None

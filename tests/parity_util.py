@@ -7,13 +7,14 @@ from paper_1305_5615_gb300 import rewl
 
 
 def make_pair(model, L, h, o, m, flatness, lnf_final, seed, q=2, couplings=None, spe=100, spf=1000, lnf0=1.0,
-              G=0, wpb=0, mode=rewl.MODE_PLAIN, entry_max_sweeps=1000, discovery_sweeps=200):
+              G=0, wpb=0, mode=rewl.MODE_PLAIN, entry_max_sweeps=1000, discovery_sweeps=200, wl_rule="flat"):
     O = OracleREWL(model, L, h, o, m, flatness, lnf_final, seed, q=q, couplings=couplings, sweeps_per_exchange=spe,
                    sweeps_per_flat_check=spf, lnf0=lnf0, entry_max_sweeps=entry_max_sweeps,
-                   discovery_sweeps=discovery_sweeps)
+                   discovery_sweeps=discovery_sweeps, wl_rule=wl_rule)
     D = rewl.REWL(model, L, h, o, m, flatness, lnf_final, seed, q=q, couplings=couplings, sweeps_per_exchange=spe,
                   sweeps_per_flat_check=spf, lnf0=lnf0, entry_max_sweeps=entry_max_sweeps,
-                  discovery_sweeps=discovery_sweeps, lanes_per_walker=G, walkers_per_block=wpb, mode=mode)
+                  discovery_sweeps=discovery_sweeps, lanes_per_walker=G, walkers_per_block=wpb, mode=mode,
+                  wl_rule=wl_rule)
     return O, D
 
 
@@ -42,6 +43,7 @@ def compare_states(O, D, where=""):
     assert np.array_equal(sg["lnf"].view(np.uint64), wo["lnf"].view(np.uint64)), where
     assert np.array_equal(sg["iteration"], wo["iteration"]), where
     assert np.array_equal(sg["done"] != 0, wo["done"] != 0), where
+    assert np.array_equal(sg["stage"], wo["phase"]), where
     assert np.array_equal(sg["wl_accept"], co["wl_accept"]), where
     assert np.array_equal(sg["near_ties"], co["near_ties"]), where
     assert np.array_equal(sg["x_tried"], co["x_tried"]), where

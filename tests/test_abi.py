@@ -45,3 +45,35 @@ def test_create_fails_cleanly_without_a_suitable_device():
     with pytest.raises(rewl.RewlError) as e:
         rewl.REWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0)
     assert e.value.status in (3, 9)
+
+
+STRUCTS = ("rewl_model", "rewl_lattice", "rewl_params", "rewl_info", "rewl_sweep_desc", "rewl_request",
+           "rewl_request_info", "rewl_server_stats", "rewl_state")
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the header's struct (gcc, plain C)."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "rewl.h"', "int main(void) {"]
+    for name in STRUCTS:
+        cls = getattr(rewl, name)
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n") if l)
+    for name in STRUCTS:
+        cls = getattr(rewl, name)
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, f)]) == getattr(cls, f).offset, (name, f)

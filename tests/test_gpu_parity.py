@@ -176,3 +176,88 @@ def test_torch_allocator_and_stream():
     assert compare_states(O, D, "torch allocator") == 0
     D.close()
     assert torch.cuda.memory_allocated() == before
+
+
+# ------------------------------------------------- the staged sweep variant
+@pytest.mark.parametrize("model,L,q,G", [("ising", 8, 2, 32), ("ising", 12, 2, 8), ("potts", 8, 10, 32), ("ea", 8, 2, 16)])
+def test_staged_variant_matches_oracle(model, L, q, G):
+    O = OracleREWL(model, L, 4, 0.75, 2, 0.8, 1e-6, 31 + L, q=q)
+    D = rewl.REWL(model, L, 4, 0.75, 2, 0.8, 1e-6, 31 + L, q=q, lanes_per_walker=G, sweep_variant=1)
+    _parity(O, D, [1, 12], "staged %s L=%d G=%d" % (model, L, G))
+
+
+# -------------------------------------------- failures made on the host side
+def test_timeout_then_resume_is_bit_exact():
+    _, A = make_pair("ising", 16, 4, 0.75, 2, 0.8, 1e-6, 23)
+    A.step(3000)
+    ref = A.state()
+    B = rewl.REWL("ising", 16, 4, 0.75, 2, 0.8, 1e-6, 23, timeout_ms=1)
+    with pytest.raises(rewl.RewlError) as e:
+        B.step(3000)
+    assert e.value.status == 4                         # REWL_ETIMEOUT, at a block boundary
+    done_sweeps = rewl.rewl_get_info(B._h)["sweep_clock"]
+    assert 0 < done_sweeps < 3000 and done_sweeps % 100 == 0
+    B.params.timeout_ms = 0
+    C = rewl.REWL("ising", 16, 4, 0.75, 2, 0.8, 1e-6, 23)
+    C.set_state(B.state())                               # resume the interrupted solve elsewhere
+    C.step(3000 - done_sweeps)
+    got = C.state()
+    for k in ("lattice", "E", "H", "lnf", "iteration"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert np.array_equal(got["lng"].view(np.uint64), ref["lng"].view(np.uint64))
+
+
+def test_allocation_failure_is_reported_and_nothing_leaks():
+    import ctypes
+    import torch
+
+    calls = {"n": 0}
+    live = {}
+
+    def alloc(nbytes, stream, user):
+        calls["n"] += 1
+        if calls["n"] > 6:           # refuse from the 7th allocation on
+            return None
+        p = torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(), stream)
+        live[p] = True
+        return p
+
+    def free(ptr, stream, user):
+        live.pop(ptr, None)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    A, F = rewl.ALLOC_FN(alloc), rewl.FREE_FN(free)
+    p = rewl.rewl_params_default()
+    p.alloc, p.free = A, F
+    with pytest.raises(rewl.RewlError) as e:
+        rewl.rewl_create(rewl.rewl_model(0, 2), rewl.rewl_lattice(2, 8, 8, 1), None, 4, 0.75, 2, 0.8, 1e-6, 0, p)
+    assert e.value.status == 2                           # REWL_ENOMEM
+    assert not live                                       # every granted block was returned
+    assert "allocation" in rewl.rewl_last_error()
+
+
+# ------------------------------------- draws prepared ahead on a second stream
+def test_prefetched_draws_match_in_kernel_draws_and_the_oracle():
+    """Ising L=32, 16 windows x 4 walkers: with the next block's draws prepared
+    on a second stream the states equal those of the in-kernel draws and of the
+    oracle; a rewind through rewl_set_state (stale prepared buffers) and a
+    replay give the same bits again."""
+    O, A = make_pair("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5)
+    B = rewl.REWL("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5, prefetch_draws=-1)
+    assert A.info["prefetch_draws"] == 1 and B.info["prefetch_draws"] == 0
+    A.step(1000)
+    B.step(1000)
+    sa, sb = A.state(), B.state()
+    for k in ("lattice", "E", "H", "lnf", "iteration"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(sa["lng"].view(np.uint64), sb["lng"].view(np.uint64))
+    O.run_blocks(10)    # the oracle to the same clock
+    assert compare_states(O, A, "prefetched 1000 sweeps") == 0
+    A.step(300)
+    A.set_state(sa)     # rewind: the prepared buffers now hold draws of later blocks
+    A.step(300)
+    B.step(300)
+    sa, sb = A.state(), B.state()
+    for k in ("lattice", "E", "H", "lnf", "iteration"):
+        assert np.array_equal(sa[k], sb[k]), k
+    assert np.array_equal(sa["lng"].view(np.uint64), sb["lng"].view(np.uint64))

@@ -99,3 +99,39 @@ def test_bad_requests():
     with pytest.raises(rewl.RewlError) as e:
         S.poll(999999)
     assert e.value.status == 8
+
+
+def test_one_shape_group_grows_and_shapes_run_side_by_side():
+    """Twelve +-J disorder realisations of one shape (more than a group's first
+    table of eight slots) beside two Ising requests of another shape, with
+    requests arriving while others run: every result equals its result alone,
+    and the sweep and trial counters equal those of the solve alone."""
+    glass = [dict(model="ea", L=6, windows=3, walkers_per_window=2, lnf_final=1e-2, seed=100 + i, q=2)
+             for i in range(12)]
+    ising = [dict(model="ising", L=8, windows=4, walkers_per_window=2, lnf_final=1e-3, seed=200 + i, q=2)
+             for i in range(2)]
+    alone = {}
+    for r in glass + ising:
+        D = rewl.REWL(r["model"], r["L"], r["windows"], 0.75, r["walkers_per_window"], 0.8, r["lnf_final"],
+                      r["seed"], q=r["q"])
+        assert D.step(0)
+        alone[r["seed"]] = (D.lng()[0], D.info["sweep_clock"], D.info["attempts"])
+        D.close()
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=16)
+    ids = {}
+    for r in ising + glass[:6]:
+        ids[r["seed"]] = _submit(S, r)
+    S.run(5)                                  # the rest arrive while these run
+    for r in glass[6:]:
+        ids[r["seed"]] = _submit(S, r)
+    for _ in range(100000):
+        st = S.run(50)
+        if st["running"] == 0 and st["queued"] == 0:
+            break
+    assert st["finished"] == len(ids) and st["failed"] == 0
+    for seed, rid in ids.items():
+        g, sweeps, attempts = alone[seed]
+        info = S.poll(rid)
+        assert info["sweeps"] == sweeps and info["attempts"] == attempts, seed
+        assert np.array_equal(S.result(rid)[0].view(np.uint64), g.view(np.uint64)), seed
+    assert st["attempts"] == sum(alone[s][2] for s in ids)
