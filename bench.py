@@ -48,19 +48,22 @@ METRIC = "spin-flip attempts/s (REWL: WL sweeps + exchange + flatness/merge)"
 # Philox4x32-10 = 10 rounds x (2 IMAD.WIDE + 2 LOP3) = 40 with the round keys
 # held in registers; site, row and column 4; neighbour loads and the dE count
 # 12; bin, window test and the fixed-point acceptance test 6; shadow, H and
-# configuration updates 4.  Total 66 (the accounting is stated in the design doc).
+# configuration updates 4.  Total 66.
 OPS_PER_ATTEMPT = 66
 LANES_PER_SM_PER_CLK = 128   # 4 schedulers x 32 lanes
 N_SM = 152
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_ising_L32_h16_m4.txt")
 
 
+SWEEP_SOURCES = ("rewl_device.cuh", "rewl_kernels.cu", "rewl_layout.h")
+
+
 def kernel_source_hash():
+    """Hash of the sources the sweep kernel is compiled from."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1305_5615_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in SWEEP_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -304,7 +307,7 @@ def run_gb300(args, wl, world, rank, local):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_sweep", "avg_launch_ms": avg_s * 1e3,
                 "attempts_per_launch": att_per_launch, "ops_per_attempt": OPS_PER_ATTEMPT,
-                "peak_basis": "152 SMs x 128 int lanes/clk x %.0f MHz (derived, see DESIGN.md)" % (f_max / 1e6),
+                "peak_basis": "152 SMs x 128 int lanes/clk x %.0f MHz (derived from unit counts and the maximum SM clock)" % (f_max / 1e6),
                 "sweep_share_of_step": sweep_ms / 1e3 / t_local if t_local > 0 else None}
 
     cpu = None
@@ -469,13 +472,188 @@ def run_served(args, world, rank, local):
                           "served": served, "plain_one_at_a_time": plain}), flush=True)
 
 
+def _first_iteration(rewl, wl, seed, max_sweeps, **kw):
+    """Runs a solve until every window has finished its first iteration (or the
+    sweep budget ends); returns (state, info, seconds)."""
+    D = rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seed, q=wl["q"], **kw)
+    t0 = time.perf_counter()
+    while True:
+        D.step(SPF)
+        st = D.state()
+        if (st["first_iter"] > 0).all() or st["sweep_clock"] >= max_sweeps:
+            break
+    el = time.perf_counter() - t0
+    info = dict(D.info)
+    D.close()
+    return st, info, el
+
+
+def run_windows_balance(args, world, rank, local):
+    """Fig. 1b against Fig. 1a: sweeps until every window has finished its
+    first WL iteration (the paper's speed-up counts the sweeps of the slowest
+    walker, Eq. (2)), with equal windows and with the run-time balanced
+    partition planned from that equal run (rewl_plan_windows)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    wl = WORKLOADS[args.base_workload]
+    eq, info_eq, t_eq = _first_iteration(rewl, wl, args.seed, args.max_sweeps)
+    starts, widths = rewl.rewl_plan_windows(eq["first_iter"], eq["win_start"], eq["win_width"], info_eq["n_bins"],
+                                            wl["h"], OVERLAP)
+    out = {"equal": None, "balanced": None}
+    for name, st, el, ww in (("equal", eq, t_eq, eq["win_width"]),):
+        fi = st["first_iter"]
+        out[name] = {"slowest_window_sweeps": int(fi.max()), "fastest_window_sweeps": int(fi[fi > 0].min()),
+                     "first_iter_sweeps": [int(x) for x in fi], "widths": [int(x) for x in ww], "seconds": el}
+    seeds = [args.seed + k for k in range(args.balance_seeds)]
+    runs = []
+    for sd in seeds:
+        b, info_b, t_b = _first_iteration(rewl, wl, sd, args.max_sweeps, window_starts=starts, window_widths=widths)
+        e, info_e, t_e = (eq, info_eq, t_eq) if sd == args.seed else _first_iteration(rewl, wl, sd, args.max_sweeps)
+        runs.append((int(e["first_iter"].max()), int(b["first_iter"].max())))
+        if sd == args.seed:
+            fi = b["first_iter"]
+            out["balanced"] = {"slowest_window_sweeps": int(fi.max()), "fastest_window_sweeps": int(fi[fi > 0].min()),
+                               "first_iter_sweeps": [int(x) for x in fi], "starts": [int(x) for x in starts],
+                               "widths": [int(x) for x in widths], "seconds": t_b}
+    ratio = float(np.mean([e / b for e, b in runs]))
+    if rank == 0:
+        print(json.dumps({"metric": "sweeps until every window finished its first WL iteration (slowest window), "
+                                    "equal vs run-time balanced windows",
+                          "value": ratio, "unit": "speed-up (equal / balanced)", "n_gpus": world,
+                          "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "windows-balance", "base": args.base_workload, "desc": wl["desc"],
+                                     "seeds": seeds, "plan_from_seed": args.seed},
+                          "per_seed_slowest_sweeps_equal_balanced": runs, "detail": out}), flush=True)
+
+
+def _exact_ising_L32():
+    """ln g of the exact 32 x 32 Ising DOS (tests/golden, written from the
+    Kaufman/Beale closed form), indexed by global bin."""
+    import math
+
+    import numpy as np
+
+    out = np.full(1025, -np.inf)
+    for line in open(os.path.join(ROOT, "tests", "golden", "ising_L32_exact_dos.txt")):
+        if line.startswith("#"):
+            continue
+        e, c = line.split()
+        c = int(c)
+        b = c.bit_length()
+        out[(int(e) + 2048) // 4] = math.log(c) if b < 1000 else math.log(c >> (b - 60)) + (b - 60) * math.log(2.0)
+    return out
+
+
+def run_rule_compare(args, world, rank, local):
+    """The two WL rules on the GPU (Ising 32 x 32, 16 windows x 4 walkers): for
+    each final ln f, the sweeps and seconds to converge and the error against
+    the exact DOS (max relative error of ln g over E <= 0 with g(E_min) = 2,
+    and the max absolute error after the best constant shift)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    ex = _exact_ising_L32()
+    fin = np.isfinite(ex)
+    half = fin & (-2048 + 4 * np.arange(1025) <= 0)
+    res = []
+    for rule in ("flat", "1/t"):
+        for k in args.rule_k:
+            D = rewl.REWL("ising", 32, 16, OVERLAP, 4, FLATNESS, 2.0 ** -k * 0.75, args.seed, wl_rule=rule)
+            t0 = time.perf_counter()
+            D.step(0)
+            el = time.perf_counter() - t0
+            g, _, _ = D.lng()
+            gn = g - g[0] + ex[0]
+            rel = float(np.max(np.abs(gn[half] - ex[half]) / ex[half]))
+            d = g[fin] - ex[fin]
+            absd = float(np.max(np.abs(d - d.mean())))
+            res.append({"rule": rule, "final_lnf": 2.0 ** -k, "sweeps": int(D.info["sweep_clock"]), "seconds": el,
+                        "max_rel_err_E_le_0": rel, "max_abs_err_shifted": absd})
+            D.close()
+    if rank == 0:
+        print(json.dumps({"metric": "error against the exact DOS and time to converge, flatness rule vs 1/t rule",
+                          "value": None, "unit": None, "n_gpus": world, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "rule-compare", "desc": WORKLOADS[DEFAULT_WORKLOAD]["desc"],
+                                     "seed": args.seed}, "runs": res}), flush=True)
+
+
+def run_time_to_dos(args, world, rank, local):
+    """Time to the converged ln g (every window at ln f_final) over seeds, the
+    served form against the plain form.  Served: all seeds submitted at once
+    to the request server (their walkers share the GPU); plain: the first
+    --tdos-plain seeds solved one after another with rewl_create/rewl_step,
+    the others modelled as their own sweep count (identical in both forms)
+    times the plain seconds per sweep measured on the solved ones, queued one
+    after another.  Reports p50/p99 of both and the result bits of the plain
+    solves against the served ones."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    wl = WORKLOADS[args.base_workload]
+    seeds = list(range(args.seed, args.seed + args.tdos_seeds))
+    S = rewl.RewlServer(device_bytes=args.server_gb << 30, max_running=len(seeds))
+    t0 = time.perf_counter()
+    ids = [S.submit(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd, q=wl["q"])
+           for sd in seeds]
+    while True:
+        st = S.run(1)
+        if st["running"] == 0 and st["queued"] == 0:
+            break
+    t_served = time.perf_counter() - t0
+    served, sweeps = [], []
+    for rid in ids:
+        inf = S.poll(rid)
+        served.append(inf["latency_ms"] / 1e3)
+        sweeps.append(inf["sweeps"])
+    plain, per_sweep, bits = [], [], []
+    for k, sd in enumerate(seeds[:args.tdos_plain]):
+        t1 = time.perf_counter()
+        D = rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd, q=wl["q"])
+        D.step(0)
+        g, _, _ = D.lng()
+        el = time.perf_counter() - t1
+        plain.append(el)
+        per_sweep.append(el / D.info["sweep_clock"])
+        bits.append(bool(np.array_equal(g.view(np.uint64), S.result(ids[k])[0].view(np.uint64))))
+        D.close()
+    sps = float(np.mean(per_sweep)) if per_sweep else None
+    svc = [plain[k] if k < len(plain) else sps * sweeps[k] for k in range(len(seeds))]
+    queued = list(np.cumsum(svc))          # all submitted at t = 0, solved one after another
+    if rank == 0:
+        print(json.dumps({"metric": "time to converged ln g (ln f_final), p50/p99 over seeds, served vs plain",
+                          "value": float(np.percentile(served, 50)), "unit": "s (served p50)", "n_gpus": world,
+                          "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "time-to-dos", "base": args.base_workload, "desc": wl["desc"],
+                                     "seeds": seeds},
+                          "served": {"wall_s": t_served, "p50_s": float(np.percentile(served, 50)),
+                                     "p99_s": float(np.percentile(served, 99)), "per_seed_s": served,
+                                     "sweeps": sweeps, "attempts_per_s": st["attempts"] / t_served},
+                          "plain": {"solved": len(plain), "solved_s": plain, "seconds_per_sweep": sps,
+                                    "service_p50_s": float(np.percentile(svc, 50)),
+                                    "service_p99_s": float(np.percentile(svc, 99)),
+                                    "queued_p50_s": float(np.percentile(queued, 50)),
+                                    "queued_p99_s": float(np.percentile(queued, 99)),
+                                    "bit_identical_to_served": bits}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["served-stream"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["served-stream", "windows-balance", "rule-compare",
+                                                                        "time-to-dos"])
     ap.add_argument("--mode", default="plain", choices=["plain", "graph"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -487,6 +665,13 @@ def main():
     ap.add_argument("--server-gb", type=int, default=64, help="served-stream: device-memory budget in GiB")
     ap.add_argument("--plain-check", type=int, default=3, help="served-stream: solve this many plain in full")
     ap.add_argument("--served-timeout", type=float, default=1200.0, help="served-stream: stop after this many seconds")
+    ap.add_argument("--base-workload", default="potts-q10-L32-h32-m16", choices=sorted(WORKLOADS),
+                    help="windows-balance, time-to-dos: the problem")
+    ap.add_argument("--balance-seeds", type=int, default=3, help="windows-balance: seeds compared")
+    ap.add_argument("--max-sweeps", type=int, default=2000000, help="windows-balance: sweep budget per run")
+    ap.add_argument("--rule-k", type=int, nargs="+", default=[16, 20], help="rule-compare: final ln f = 2^-k")
+    ap.add_argument("--tdos-seeds", type=int, default=8, help="time-to-dos: seeds")
+    ap.add_argument("--tdos-plain", type=int, default=1, help="time-to-dos: seeds also solved plain in full")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -496,6 +681,24 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the served stream has no CPU reference arm"}))
             return
         run_served(args, world, rank, local)
+        return
+    if args.workload == "time-to-dos":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "time-to-DOS over seeds has no CPU reference arm"}))
+            return
+        run_time_to_dos(args, world, rank, local)
+        return
+    if args.workload == "rule-compare":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the rule comparison has no CPU reference arm"}))
+            return
+        run_rule_compare(args, world, rank, local)
+        return
+    if args.workload == "windows-balance":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the window-balance comparison has no CPU reference arm"}))
+            return
+        run_windows_balance(args, world, rank, local)
         return
     wl = WORKLOADS[args.workload]
     if world > 1 and args.impl == "gb300":

@@ -62,7 +62,7 @@ typedef struct {
   int32_t q;
 } rewl_model;
 
-/* Lattice: dim must be 2, Lx == Ly == L with 2 <= L <= 128 (L even for +-J),
+/* Lattice: dim must be 2, Lx == Ly == L with 2 <= L <= 256 (L even for +-J),
  * periodic must be 1. */
 typedef struct {
   int32_t dim, Lx, Ly, periodic;
@@ -92,13 +92,24 @@ typedef struct {
   void* alloc_user;
   int32_t profile;               /* 1 = time every sweep launch with CUDA events on the solve's stream
                                     (plain mode); read back through rewl_info */
-  int32_t sweep_variant;         /* sweep kernel form, identical results: 0 = two-deep chain (default),
-                                    1 = staged one-deep chain */
-  int32_t prefetch_draws;        /* 0 = automatic: in plain mode the draws of the next block (sites, ln u,
-                                    conflict masks) are prepared on a second stream while the current block
-                                    runs, when both buffers fit in 1 GiB; -1 = never */
+  int32_t sweep_variant;         /* sweep kernel form, identical results: REWL_SWEEP_AUTO (default: the
+                                    ring form when the solve has at most 8 walkers per SM and lanes / walkers
+                                    per block are not forced, else the chain form), REWL_SWEEP_CHAIN
+                                    (two-deep chain), REWL_SWEEP_STAGED (staged one-deep chain),
+                                    REWL_SWEEP_RING (the chain with its draws made by a second, producer warp
+                                    of the CTA; 32 lanes and one walker per CTA) */
+  int32_t prefetch_draws;        /* 1 = in plain mode with variant 0 the draws of the next block (sites,
+                                    ln u, conflict masks) are prepared on a second stream while the current
+                                    block runs, when both buffers fit in 1 GiB; 0 = no (default: kernels
+                                    running beside the sweep slow its chains) */
   int32_t wl_rule;               /* how ln f falls (the WL "update/convergence rule"): REWL_RULE_FLAT or
                                     REWL_RULE_ONE_OVER_T; see below */
+  const int32_t* window_starts;  /* NULL: the equal partition of Fig. 1a from `windows` and `overlap`.
+                                    Else `windows` first bins (global, 0-based) of an explicit partition,
+                                    e.g. the run-time balanced one of Fig. 1b from rewl_plan_windows;
+                                    read at rewl_create.  Must cover bins 0 .. n_bins-1 with widths >= 3,
+                                    strictly increasing starts and ends, neighbours sharing >= 1 bin */
+  const int32_t* window_widths;  /* `windows` widths in bins, with window_starts (both or neither) */
 } rewl_params;
 
 /*
@@ -116,6 +127,7 @@ typedef struct {
  * ln f < lnf_final.
  */
 enum { REWL_RULE_FLAT = 0, REWL_RULE_ONE_OVER_T = 1 };
+enum { REWL_SWEEP_AUTO = -1, REWL_SWEEP_CHAIN = 0, REWL_SWEEP_STAGED = 1, REWL_SWEEP_RING = 2 };
 
 /* Fills *p with the defaults above. */
 void rewl_params_default(rewl_params* p);
@@ -207,6 +219,7 @@ typedef struct {
   int64_t h2d_bytes;         /* bytes copied host -> device by this handle so far */
   int64_t d2h_bytes;         /* bytes copied device -> host by this handle so far */
   int32_t prefetch_draws;    /* 1 when the next block's draws are prepared on a second stream */
+  int32_t sweep_variant;     /* the sweep form in use (REWL_SWEEP_CHAIN, _STAGED or _RING) */
 } rewl_info;
 
 rewl_status rewl_get_info(rewl_handle h, rewl_info* info);
@@ -245,11 +258,35 @@ typedef struct {
   int64_t sweep_clock;
   int64_t exchange_rounds;
   int32_t* stage;       /* [windows] 1/t rule stage (0 or 1); optional, NULL reads as all 0 */
+  int32_t* win_width;   /* [windows] bins of each window (read only; lng/H rows have window_bins =
+                           the largest width, bins past a window's width stay 0) */
+  int64_t* first_iter;  /* [windows] sweep clock at which the window's first merge happened, -1 before;
+                           optional on set */
 } rewl_state;
 
 /* Copies the device state into the caller's buffers.  Errors: REWL_EINVAL,
  * REWL_ECUDA. */
 rewl_status rewl_get_state(rewl_handle h, rewl_state* st);
+
+/*
+ * rewl_plan_windows -- the run-time balanced partition of Fig. 1b: windows
+ * sized so that each finishes its first WL iteration after about the same
+ * number of sweeps, estimated from a pre-run (the speed-up paragraph).  The
+ * paper gives no formula; reading: a window's first iteration is a diffusive
+ * walk lasting (sum over its bins of rho(b))^2; pre-run window a, which first
+ * merged after first_iter_sweeps[a] sweeps (rewl_state.first_iter) and has
+ * pre_widths[a] bins, gives rho_a = sqrt(first_iter_sweeps[a]) /
+ * pre_widths[a]; rho(b) is the mean of rho_a over the pre-run windows holding
+ * bin b.  The new `windows` windows are the equal partition of Fig. 1a with
+ * overlap o laid out in the coordinate U(b) = rho(0) + ... + rho(b-1): each
+ * carries the same sum of rho.  Host-only arithmetic (no device).  Output:
+ * starts / widths, `windows` values each, for rewl_params.window_starts /
+ * window_widths.  Errors: REWL_EINVAL (a pre-run window without a first
+ * merge, a partition that would not pass rewl_create's checks).
+ */
+rewl_status rewl_plan_windows(const int64_t* first_iter_sweeps, const int32_t* pre_starts, const int32_t* pre_widths,
+                              int32_t pre_windows, int32_t n_bins, int32_t windows, double overlap, int32_t* starts,
+                              int32_t* widths);
 
 /* Restores a state previously read from a handle created with the same
  * arguments (checkpoint / resume); lattice, E, lng, H, lnf, iteration, done

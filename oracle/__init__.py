@@ -49,7 +49,8 @@ def build(force=False):
 class _Params(ctypes.Structure):
     _fields_ = [("sweeps_per_exchange", ctypes.c_int), ("sweeps_per_flat_check", ctypes.c_int),
                 ("lnf0", ctypes.c_double), ("entry_max_sweeps", ctypes.c_int),
-                ("discovery_sweeps", ctypes.c_int), ("wl_rule", ctypes.c_int)]
+                ("discovery_sweeps", ctypes.c_int), ("wl_rule", ctypes.c_int),
+                ("window_starts", ctypes.c_void_p), ("window_widths", ctypes.c_void_p)]
 
 
 def lib():
@@ -68,6 +69,7 @@ def lib():
         L.orc_info.argtypes = [P, P]
         L.orc_get_windows.argtypes = [P, P, P, P, P]
         L.orc_get_phase.argtypes = [P, P]
+        L.orc_get_window_layout.argtypes = [P, P, P]
         L.orc_walker_all_seen.argtypes = [P, ctypes.c_int]
         L.orc_walker_all_seen.restype = ctypes.c_int
         L.orc_get_walkers.argtypes = [P, P, P, P, P]
@@ -103,13 +105,18 @@ class OracleREWL:
 
     def __init__(self, model, L, windows, overlap, walkers_per_window, flatness, lnf_final, seed, q=2,
                  couplings=None, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
-                 entry_max_sweeps=1000, discovery_sweeps=200, wl_rule=0):
+                 entry_max_sweeps=1000, discovery_sweeps=200, wl_rule=0, window_starts=None, window_widths=None):
         if isinstance(model, str):
             model = MODEL_NAMES[model]
         if isinstance(wl_rule, str):
             wl_rule = WL_RULES[wl_rule]
         self._lib = lib()
         p = _Params(sweeps_per_exchange, sweeps_per_flat_check, lnf0, entry_max_sweeps, discovery_sweeps, wl_rule)
+        if window_starts is not None:
+            self._ws = np.ascontiguousarray(window_starts, dtype=np.int32)
+            self._ww = np.ascontiguousarray(window_widths, dtype=np.int32)
+            assert self._ws.shape == (windows,) and self._ww.shape == (windows,)
+            p.window_starts, p.window_widths = self._ws.ctypes.data, self._ww.ctypes.data
         h = ctypes.c_void_p()
         cpl = None
         if couplings is not None:
@@ -152,9 +159,13 @@ class OracleREWL:
         it = np.zeros(h, np.int32)
         done = np.zeros(h, np.int32)
         phase = np.zeros(h, np.int32)
+        width = np.zeros(h, np.int32)
+        first = np.zeros(h, np.int64)
         self._lib.orc_get_windows(self._h, _ptr(start), _ptr(lnf), _ptr(it), _ptr(done))
         self._lib.orc_get_phase(self._h, _ptr(phase))
-        return {"start": start, "lnf": lnf, "iteration": it, "done": done, "phase": phase}
+        self._lib.orc_get_window_layout(self._h, _ptr(width), _ptr(first))
+        return {"start": start, "lnf": lnf, "iteration": it, "done": done, "phase": phase, "width": width,
+                "first_iter": first}
 
     def walkers(self):
         n = self.h * self.m
@@ -214,5 +225,5 @@ class OracleREWL:
     def joined_lng(self):
         from .join import join_windows, normalise
         win = self.windows()
-        g = join_windows(self.window_lng(), win["start"], self.w, self.n_bins)
+        g = join_windows(self.window_lng(), win["start"], win["width"], self.n_bins)
         return normalise(g, self.N, self.q)

@@ -25,12 +25,15 @@ import numpy as np
 
 def join_windows(lng_windows, starts, w, n_bins):
     """lng_windows[a][b] is window a's ln g at its local bin b (0 = never
-    visited); starts[a] its first global bin.  Returns the joined, not yet
-    normalised ln g over n_bins global bins (-inf where not visited)."""
+    visited); starts[a] its first global bin; w the width of every window, or
+    a sequence of per-window widths (unequal, run-time balanced windows).
+    Returns the joined, not yet normalised ln g over n_bins global bins (-inf
+    where not visited)."""
     h = len(starts)
+    widths = [int(w)] * h if np.ndim(w) == 0 else [int(x) for x in w]
     out = np.full(n_bins, -np.inf)
     first = np.asarray(lng_windows[0], dtype=np.float64)
-    for b in range(w):
+    for b in range(widths[0]):
         if first[b] > 0.0:
             out[starts[0] + b] = first[b]
     shift_prev = 0.0
@@ -38,7 +41,7 @@ def join_windows(lng_windows, starts, w, n_bins):
         A = np.asarray(lng_windows[a], dtype=np.float64)
         B = np.asarray(lng_windows[a + 1], dtype=np.float64)
         sa, sb = int(starts[a]), int(starts[a + 1])
-        lo, hi = sb, sa + w - 1          # global overlap [lo, hi]
+        lo, hi = sb, sa + widths[a] - 1  # global overlap [lo, hi]
         best, best_b = None, None
         for g in range(lo + 1, hi):      # interior overlap bins
             ia, ib = g - sa, g - sb
@@ -57,7 +60,7 @@ def join_windows(lng_windows, starts, w, n_bins):
         if best_b is None:
             raise ValueError("windows %d and %d share no visited bin" % (a, a + 1))
         shift = (A[best_b - sa] + shift_prev) - B[best_b - sb]
-        for g in range(best_b + 1, sb + w):
+        for g in range(best_b + 1, sb + widths[a + 1]):
             v = B[g - sb]
             out[g] = v + shift if v > 0 else -np.inf
         shift_prev = shift

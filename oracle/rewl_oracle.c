@@ -142,12 +142,31 @@ static int bin_of(const orc_rewl* R, int E) { return (E - R->e_min) / R->e_step;
 
 /* Window width w = ceil(B / (1 + (h-1)(1-o))) bins; starts are k(B-w)/(h-1)
  * rounded half up, so the first window starts at bin 0 and the last ends at
- * bin B-1.  (The paper gives no rounding rule; this is the reading used.) */
+ * bin B-1.  (The paper gives no rounding rule; this is the reading used.)
+ * A partition given explicitly (Fig. 1b: run-time balanced windows of
+ * unequal width) must start at bin 0, end at bin B-1, have widths >= 3,
+ * strictly increasing starts and ends, and neighbours sharing >= 1 bin. */
 static int make_windows(orc_rewl* R) {
   int B = R->n_bins, h = R->h;
+  if (R->params.window_starts) {
+    const int32_t* st = R->params.window_starts;
+    const int32_t* wd = R->params.window_widths;
+    if (!wd || st[0] != 0 || st[h - 1] + wd[h - 1] != B) return ORC_EINVAL;
+    R->w = 0;
+    for (int k = 0; k < h; ++k) {
+      if (wd[k] < 3 || st[k] < 0 || st[k] + wd[k] > B) return ORC_EINVAL;
+      if (k > 0 && (st[k] <= st[k - 1] || st[k] + wd[k] <= st[k - 1] + wd[k - 1] || st[k] > st[k - 1] + wd[k - 1] - 1))
+        return ORC_EINVAL;
+      R->win_start[k] = st[k];
+      R->win_width[k] = wd[k];
+      if (wd[k] > R->w) R->w = wd[k];
+    }
+    return ORC_OK;
+  }
   if (h == 1) {
     R->w = B;
     R->win_start[0] = 0;
+    R->win_width[0] = B;
     return ORC_OK;
   }
   double wd = ceil((double)B / (1.0 + (double)(h - 1) * (1.0 - R->overlap)));
@@ -158,6 +177,7 @@ static int make_windows(orc_rewl* R) {
   for (int k = 0; k < h; ++k) {
     int64_t num = 2 * (int64_t)k * (int64_t)(B - w) + (h - 1);
     R->win_start[k] = (int)(num / (2 * (int64_t)(h - 1)));
+    R->win_width[k] = w;
   }
   for (int k = 0; k + 1 < h; ++k)
     if (R->win_start[k + 1] > R->win_start[k] + w - 1) return ORC_EINVAL; /* neighbours must overlap */
@@ -165,7 +185,7 @@ static int make_windows(orc_rewl* R) {
 }
 
 static int win_lo_E(const orc_rewl* R, int a) { return R->e_min + R->win_start[a] * R->e_step; }
-static int win_hi_E(const orc_rewl* R, int a) { return R->e_min + (R->win_start[a] + R->w - 1) * R->e_step; }
+static int win_hi_E(const orc_rewl* R, int a) { return R->e_min + (R->win_start[a] + R->win_width[a] - 1) * R->e_step; }
 static int in_window(const orc_rewl* R, int a, int E) { return E >= win_lo_E(R, a) && E <= win_hi_E(R, a); }
 
 /* ------------------------------------------------------------------------ */
@@ -251,7 +271,7 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   *out = NULL;
   orc_params P;
   if (params) P = *params; else orc_default_params(&P);
-  if (model < 0 || model > 2 || L < 2 || L > 128 || h < 1 || m < 1 || h * m > (1 << 20)) return ORC_EINVAL;
+  if (model < 0 || model > 2 || L < 2 || L > 256 || h < 1 || m < 1 || h * m > (1 << 20)) return ORC_EINVAL;
   if (model == ORC_POTTS && (q < 2 || q > 16)) return ORC_EINVAL;
   if (model == ORC_EA && (L % 2) != 0) return ORC_EINVAL;
   if (!(overlap > 0.0 && overlap < 1.0) || !(flatness > 0.0 && flatness <= 1.0) || !(lnf_final > 0.0)) return ORC_EINVAL;
@@ -296,6 +316,9 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   R->entry_t = (uint64_t*)calloc((size_t)n_walkers, sizeof(uint64_t));
   R->seed_config = (uint8_t*)calloc((size_t)N, 1);
   R->win_start = (int*)calloc((size_t)h, sizeof(int));
+  R->win_width = (int*)calloc((size_t)h, sizeof(int));
+  R->first_iter = (int64_t*)malloc((size_t)h * sizeof(int64_t));
+  for (int a = 0; a < h; ++a) R->first_iter[a] = -1;
   R->lnf = (double*)calloc((size_t)h, sizeof(double));
   R->iter = (int*)calloc((size_t)h, sizeof(int));
   R->done = (int*)calloc((size_t)h, sizeof(int));
@@ -352,7 +375,7 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
 void orc_destroy(orc_rewl* R) {
   if (!R) return;
   free(R->Jr); free(R->Jd); free(R->spins); free(R->E); free(R->entry_t); free(R->seed_config);
-  free(R->win_start); free(R->lnf); free(R->iter); free(R->done); free(R->phase); free(R->lng); free(R->H);
+  free(R->win_start); free(R->win_width); free(R->first_iter); free(R->lnf); free(R->iter); free(R->done); free(R->phase); free(R->lng); free(R->H);
   free(R->wl_accept); free(R->near_ties); free(R->x_tried); free(R->x_accepted);
   free(R);
 }
@@ -467,7 +490,7 @@ int orc_walker_is_flat(const orc_rewl* R, int W) {
   uint64_t S = 0;
   uint32_t hmin = 0xffffffffu;
   int n = 0;
-  for (int b = 0; b < R->w; ++b) {
+  for (int b = 0; b < R->win_width[W / R->m]; ++b) {
     if (lng[b] > 0.0) {
       ++n;
       S += H[b];
@@ -482,7 +505,8 @@ int orc_walker_is_flat(const orc_rewl* R, int W) {
 /* order) and handed back to all of them; H is reset.                        */
 static void merge_window(orc_rewl* R, int a) {
   int m = R->m;
-  for (int b = 0; b < R->w; ++b) {
+  if (R->iter[a] == 0) R->first_iter[a] = (int64_t)R->sweep_clock; /* end of the first iteration */
+  for (int b = 0; b < R->win_width[a]; ++b) {
     double sum = lng_of(R, a * m)[b];
     for (int k = 1; k < m; ++k) sum = sum + lng_of(R, a * m + k)[b];
     double mean = sum / (double)m;
@@ -514,7 +538,7 @@ static void flatness_and_merge(orc_rewl* R, int a) {
 /* again (H(E) > 0 everywhere); once a halving would take ln f below 1/t,   */
 /* ln f follows 1/t, where t is the Monte Carlo time in trials per energy   */
 /* level.  Reading used here (the paper gives no details):                  */
-/*   - t of window a = (trials per walker) / w = sweep_clock * N / w;       */
+/*   - t of window a = (trials per walker) / w_a = sweep_clock * N / w_a;   */
 /*   - stage 0 test at each check: every walker of the window has H > 0 in  */
 /*     every bin it has visited (ln g > 0); then the window merges and      */
 /*     either halves ln f = 2^-k, or, when 2^-(k+1) < 1/t (i.e.             */
@@ -529,7 +553,7 @@ int orc_walker_all_seen(const orc_rewl* R, int W) {
   const double* lng = R->lng + (size_t)W * R->w;
   const uint32_t* H = R->H + (size_t)W * R->w;
   int n = 0;
-  for (int b = 0; b < R->w; ++b) {
+  for (int b = 0; b < R->win_width[W / R->m]; ++b) {
     if (lng[b] > 0.0) {
       ++n;
       if (H[b] == 0u) return 0;
@@ -545,7 +569,7 @@ static void one_over_t_step(orc_rewl* R, int a) {
   int k = 1 - e2;
   uint64_t trials = R->sweep_clock * (uint64_t)R->N;
   /* w * 2^(k+1): t >= 2^(k+1) iff trials >= next (beyond 2^47 trials per level: never) */
-  uint64_t next = k + 1 < 48 ? (uint64_t)R->w << (k + 1) : UINT64_MAX;
+  uint64_t next = k + 1 < 48 ? (uint64_t)R->win_width[a] << (k + 1) : UINT64_MAX;
   if (R->phase[a] == 0) {
     for (int j = 0; j < m; ++j)
       if (!orc_walker_all_seen(R, a * m + j)) return;
@@ -610,6 +634,13 @@ void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* it
     if (lnf) lnf[a] = R->lnf[a];
     if (iter) iter[a] = R->iter[a];
     if (done) done[a] = R->done[a];
+  }
+}
+
+void orc_get_window_layout(const orc_rewl* R, int32_t* width, int64_t* first_iter) {
+  for (int a = 0; a < R->h; ++a) {
+    if (width) width[a] = R->win_width[a];
+    if (first_iter) first_iter[a] = R->first_iter[a];
   }
 }
 

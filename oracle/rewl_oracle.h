@@ -17,6 +17,8 @@ typedef struct {
   int entry_max_sweeps;       /* budget of each greedy entry walk (1000 sweeps) */
   int discovery_sweeps;       /* +-J only: zero-temperature descent that fixes the energy range (200) */
   int wl_rule;                /* 0: flatness rule (f -> sqrt f on flat H); 1: the 1/t rule */
+  const int32_t* window_starts; /* h first bins, or NULL for the equal partition (Fig. 1a) */
+  const int32_t* window_widths; /* h widths in bins (with window_starts) */
 } orc_params;
 
 typedef struct orc_rewl {
@@ -28,6 +30,8 @@ typedef struct orc_rewl {
   uint64_t seed;
   orc_params params;
   int* win_start;             /* first global bin of each window */
+  int* win_width;             /* bins of each window (w is the largest) */
+  int64_t* first_iter;        /* sweep clock of each window's first merge, -1 before it */
   double* lnf;
   int *iter, *done;
   int* phase;                 /* 1/t rule: 0 while ln f is halved on the histogram test, 1 once it follows 1/t */
@@ -53,6 +57,7 @@ int orc_walker_is_flat(const orc_rewl* R, int W);
 void orc_info(const orc_rewl* R, int64_t* info);
 void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* iter, int32_t* done);
 void orc_get_phase(const orc_rewl* R, int32_t* phase);
+void orc_get_window_layout(const orc_rewl* R, int32_t* width, int64_t* first_iter);
 int orc_walker_all_seen(const orc_rewl* R, int W);
 void orc_get_walkers(const orc_rewl* R, uint8_t* spins, int32_t* E, double* lng, uint32_t* H);
 void orc_get_couplings(const orc_rewl* R, int8_t* J);

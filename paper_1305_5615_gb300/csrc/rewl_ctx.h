@@ -18,11 +18,12 @@ struct rewl_ctx {
   rewl_params params{};
   double overlap = 0.0;
   int e_max = 0;
-  std::vector<int32_t> win_start;
+  std::vector<int32_t> win_start, win_width;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<void*> allocations;
   int G = 32, wpb = 1;
+  int n_sm = 152;               // streaming multiprocessors of the device
   int n_active = 0;
   int n_done = 0;
   uint64_t sweep_clock = 0, xround = 0;

@@ -81,10 +81,12 @@ rewl_ctx::~rewl_ctx() {
 // Energy windows: w = ceil(B / (1 + (h-1)(1-o))) bins, window k starting at
 // k(B-w)/(h-1) rounded half up (paper, Fig. 1a: equal-size windows, overlap o).
 // ---------------------------------------------------------------------------
-static rewl_status make_windows(int B, int h, double o, int* w_out, std::vector<int32_t>& start) {
+static rewl_status make_windows(int B, int h, double o, int* w_out, std::vector<int32_t>& start,
+                                std::vector<int32_t>& width) {
   start.assign(h, 0);
   if (h == 1) {
     *w_out = B;
+    width.assign(1, B);
     return REWL_OK;
   }
   int w = (int)std::ceil((double)B / (1.0 + (double)(h - 1) * (1.0 - o)));
@@ -94,6 +96,22 @@ static rewl_status make_windows(int B, int h, double o, int* w_out, std::vector<
   for (int k = 0; k + 1 < h; ++k)
     if (start[k + 1] > start[k] + w - 1) return fail(REWL_EINVAL, "windows %d and %d do not overlap", k, k + 1);
   *w_out = w;
+  width.assign(h, w);
+  return REWL_OK;
+}
+
+// An explicit partition (Fig. 1b: run-time balanced windows of unequal width):
+// from bin 0 to bin B-1, widths >= 3, starts and ends strictly increasing,
+// neighbours sharing at least one bin.
+static rewl_status check_windows(int B, int h, const int32_t* st, const int32_t* wd) {
+  if (st[0] != 0 || (int64_t)st[h - 1] + wd[h - 1] != B)
+    return fail(REWL_EINVAL, "the windows must cover bins 0 .. %d", B - 1);
+  for (int k = 0; k < h; ++k) {
+    if (wd[k] < 3 || st[k] < 0 || (int64_t)st[k] + wd[k] > B) return fail(REWL_EINVAL, "window %d: start %d width %d", k, st[k], wd[k]);
+    if (k > 0 && (st[k] <= st[k - 1] || st[k] + wd[k] <= st[k - 1] + wd[k - 1]))
+      return fail(REWL_EINVAL, "windows %d and %d are not ordered", k - 1, k);
+    if (k > 0 && st[k] > st[k - 1] + wd[k - 1] - 1) return fail(REWL_EINVAL, "windows %d and %d do not overlap", k - 1, k);
+  }
   return REWL_OK;
 }
 
@@ -125,6 +143,10 @@ static void choose_config(rewl_ctx* c, int n_sm) {
     wpb = std::max(1, std::min(wpb, spread));
   }
   wpb = std::max(1, std::min(wpb, 256 / G));
+  if (c->params.sweep_variant == kSweepRing) {  // one walker per CTA on a whole warp, plus its producer warp
+    G = 32;
+    wpb = 1;
+  }
   c->G = G;
   c->wpb = wpb;
 }
@@ -191,6 +213,7 @@ void rewl_params_default(rewl_params* p) {
   p->entry_max_sweeps = 1000;
   p->discovery_sweeps = 200;
   p->mode = REWL_MODE_PLAIN;
+  p->sweep_variant = REWL_SWEEP_AUTO;
 }
 
 const char* rewl_status_str(rewl_status s) {
@@ -231,7 +254,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   if (lattice->dim != 2 || lattice->Lx != lattice->Ly || lattice->periodic != 1)
     return fail(REWL_EINVAL, "only 2D periodic square lattices are supported");
   const int L = lattice->Lx;
-  if (L < 2 || L > 128) return fail(REWL_EINVAL, "L=%d not in [2,128]", L);
+  if (L < 2 || L > 256) return fail(REWL_EINVAL, "L=%d not in [2,256]", L);
   if (kind == REWL_EA_PM_J && (L % 2)) return fail(REWL_EINVAL, "+-J needs an even L");
   if (kind != REWL_EA_PM_J && couplings) return fail(REWL_EINVAL, "couplings are only taken by the +-J model");
   if (windows < 1 || walkers_per_window < 1 || walkers_per_window > 4096 ||
@@ -253,9 +276,15 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   if (prm.walkers_per_block < 0 || (G && prm.walkers_per_block * G > 256))
     return fail(REWL_EINVAL, "walkers_per_block %d", prm.walkers_per_block);
   if (prm.mode != REWL_MODE_PLAIN && prm.mode != REWL_MODE_GRAPH) return fail(REWL_EINVAL, "mode %d", prm.mode);
-  if (prm.sweep_variant != 0 && prm.sweep_variant != 1) return fail(REWL_EINVAL, "sweep_variant %d", prm.sweep_variant);
+  if (prm.sweep_variant < REWL_SWEEP_AUTO || prm.sweep_variant > kSweepRing)
+    return fail(REWL_EINVAL, "sweep_variant %d", prm.sweep_variant);
+  if (prm.sweep_variant == kSweepRing && ((prm.lanes_per_walker != 0 && prm.lanes_per_walker != 32) ||
+                                          prm.walkers_per_block > 1))
+    return fail(REWL_EINVAL, "the ring variant runs 32 lanes and one walker per CTA");
   if (prm.wl_rule != REWL_RULE_FLAT && prm.wl_rule != REWL_RULE_ONE_OVER_T) return fail(REWL_EINVAL, "wl_rule %d", prm.wl_rule);
-  if (prm.prefetch_draws != 0 && prm.prefetch_draws != -1) return fail(REWL_EINVAL, "prefetch_draws %d", prm.prefetch_draws);
+  if ((prm.window_starts == nullptr) != (prm.window_widths == nullptr))
+    return fail(REWL_EINVAL, "window_starts and window_widths go together");
+  if (prm.prefetch_draws != 0 && prm.prefetch_draws != 1) return fail(REWL_EINVAL, "prefetch_draws %d", prm.prefetch_draws);
   if (couplings)
     for (int i = 0; i < 2 * L * L; ++i)
       if (couplings[i] != 1 && couplings[i] != -1) return fail(REWL_EINVAL, "coupling %d is %d", i, couplings[i]);
@@ -294,7 +323,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
       return bail(fail(REWL_ECUDA, "cudaStreamCreate failed"));
     c->own_stream = true;
   }
-  if (cudaMallocHost(&c->h_n_done, sizeof(int32_t)) != cudaSuccess) return bail(fail(REWL_ENOMEM, "pinned alloc"));
+  if (cudaMallocHost(&c->h_n_done, 2 * sizeof(int32_t)) != cudaSuccess) return bail(fail(REWL_ENOMEM, "pinned alloc"));
 
   // couplings: given, or drawn with p = 1/2 (bond b = 2i + d of site i, bit b
   // of the coupling stream), packed as bit planes (bit 1 = J = -1)
@@ -326,11 +355,13 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   S.J = (uint32_t*)c->dalloc(sizeof(uint32_t) * nJ, &st);
   S.E = (int32_t*)c->dalloc(sizeof(int32_t) * nW, &st);
   S.win_start = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
+  S.win_width = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
+  S.first_iter = (int64_t*)c->dalloc(sizeof(int64_t) * P.h, &st);
   S.lnf = (double*)c->dalloc(sizeof(double) * P.h, &st);
   S.iter = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.done = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.stage = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
-  S.n_done = (int32_t*)c->dalloc(sizeof(int32_t), &st);
+  S.n_done = (int32_t*)c->dalloc(2 * sizeof(int32_t), &st);  // [0] windows done, [1] the error word
   S.wl_accept = (uint64_t*)c->dalloc(sizeof(uint64_t) * nW, &st);
   S.near_ties = (uint64_t*)c->dalloc(sizeof(uint64_t) * nW, &st);
   S.exact_tests = (uint64_t*)c->dalloc(sizeof(uint64_t) * nW, &st);
@@ -349,7 +380,8 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
     if (e_ != cudaSuccess) return bail(fail(REWL_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)));        \
   } while (0)
   BAIL_CUDA(h2d(c, S.J, Jbits.data(), sizeof(uint32_t) * nJ));
-  BAIL_CUDA(cudaMemsetAsync(S.n_done, 0, sizeof(int32_t), s));
+  S.error = S.n_done + 1;
+  BAIL_CUDA(cudaMemsetAsync(S.n_done, 0, 2 * sizeof(int32_t), s));
   BAIL_CUDA(cudaMemsetAsync(S.iter, 0, sizeof(int32_t) * P.h, s));
   BAIL_CUDA(cudaMemsetAsync(S.done, 0, sizeof(int32_t) * P.h, s));
   BAIL_CUDA(cudaMemsetAsync(S.stage, 0, sizeof(int32_t) * P.h, s));
@@ -387,13 +419,26 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
                               cudaMemcpyDeviceToDevice, s));
   }
   P.n_bins = (c->e_max - P.e_min) / P.e_step + 1;
-  st = make_windows(P.n_bins, P.h, overlap, &P.w, c->win_start);
-  if (st != REWL_OK) return bail(st);
+  if (prm.window_starts) {
+    st = check_windows(P.n_bins, P.h, prm.window_starts, prm.window_widths);
+    if (st != REWL_OK) return bail(st);
+    c->win_start.assign(prm.window_starts, prm.window_starts + P.h);
+    c->win_width.assign(prm.window_widths, prm.window_widths + P.h);
+    P.w = *std::max_element(c->win_width.begin(), c->win_width.end());
+  } else {
+    st = make_windows(P.n_bins, P.h, overlap, &P.w, c->win_start, c->win_width);
+    if (st != REWL_OK) return bail(st);
+  }
   S.lng = (double*)c->dalloc(sizeof(double) * (size_t)nW * P.w, &st);
   S.H = (uint32_t*)c->dalloc(sizeof(uint32_t) * (size_t)nW * P.w, &st);
   if (st != REWL_OK) return bail(st);
   std::vector<double> lnf(P.h, prm.lnf0);
   BAIL_CUDA(h2d(c, S.win_start, c->win_start.data(), sizeof(int32_t) * P.h));
+  BAIL_CUDA(h2d(c, S.win_width, c->win_width.data(), sizeof(int32_t) * P.h));
+  {
+    const std::vector<int64_t> none(P.h, -1);
+    BAIL_CUDA(h2d(c, S.first_iter, none.data(), sizeof(int64_t) * P.h));
+  }
   BAIL_CUDA(h2d(c, S.lnf, lnf.data(), sizeof(double) * P.h));
   BAIL_CUDA(cudaMemsetAsync(S.lng, 0, sizeof(double) * (size_t)nW * P.w, s));
   BAIL_CUDA(cudaMemsetAsync(S.H, 0, sizeof(uint32_t) * (size_t)nW * P.w, s));
@@ -406,14 +451,23 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   int dev = 0, n_sm = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (c->params.sweep_variant == REWL_SWEEP_AUTO) {
+    // latency-bound solves (few walkers: each gets a whole warp on its own SM) run the chain with a
+    // producer warp; many walkers share SMs, where the producer's issue slots would come out of
+    // other walkers' chains, and run the plain chain
+    const bool own_sm = P.n_walkers <= 8 * n_sm && (prm.lanes_per_walker == 0 || prm.lanes_per_walker == 32) &&
+                        prm.walkers_per_block <= 1;
+    c->params.sweep_variant = own_sm ? kSweepRing : kSweepChain;
+  }
   choose_config(c, n_sm);
+  c->n_sm = n_sm;
   BAIL_CUDA(prepare_sweep(c->G, P.model));
   // Draws prepared ahead on the idle SMs: plain mode, chain kernel, G >= 8, both buffers within 1 GiB.
   {
     const uint64_t n_att = (uint64_t)prm.sweeps_per_exchange * P.N;
     const uint64_t stride = (n_att + 31) / 32 * 32;
     const uint64_t bytes = (uint64_t)P.n_walkers * stride * sizeof(PreTrial);
-    if (prm.prefetch_draws == 0 && prm.mode == REWL_MODE_PLAIN && prm.sweep_variant == kSweepChain && c->G >= 8 &&
+    if (prm.prefetch_draws == 1 && prm.mode == REWL_MODE_PLAIN && c->params.sweep_variant == kSweepChain && c->G >= 8 &&
         2 * bytes <= (1ull << 30)) {
       c->pre_stride = (uint32_t)stride;
       c->pre_buf[0] = (PreTrial*)c->dalloc(bytes, &st);
@@ -427,9 +481,9 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
       c->pre_on = true;
     }
   }
-  if (sweep_smem_bytes(P, c->wpb, c->G, prm.sweep_variant) > 227 * 1024)
+  if (sweep_smem_bytes(P, c->wpb, c->G, c->params.sweep_variant) > 227 * 1024)
     return bail(fail(REWL_EINVAL, "a walker needs %zu bytes of shared memory (window of %d bins)",
-                     sweep_smem_bytes(P, 1, c->G, prm.sweep_variant), P.w));
+                     sweep_smem_bytes(P, 1, c->G, c->params.sweep_variant), P.w));
   st = upload_active(c);
   if (st != REWL_OK) return bail(st);
 #undef BAIL_CUDA
@@ -454,7 +508,7 @@ static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
     const int k = c->pre_cur;
     if (c->pre_t0[k] != t0) {
       CUDA_TRY(cudaStreamWaitEvent(c->pre_stream, c->ev_used[k], 0));
-      CUDA_TRY(launch_precompute(c->G, c->P, t0, A.n_att, c->pre_stride, c->pre_buf[k], c->pre_stream));
+      CUDA_TRY(launch_precompute(c->G, c->P, t0, A.n_att, c->pre_stride, c->pre_buf[k], c->n_sm, c->pre_stream));
       CUDA_TRY(cudaEventRecord(c->ev_pre[k], c->pre_stream));
       c->pre_t0[k] = t0;
     }
@@ -481,7 +535,7 @@ static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
     const uint64_t t0n = (c->sweep_clock + (uint64_t)c->params.sweeps_per_exchange) * (uint64_t)c->P.N;
     CUDA_TRY(cudaEventRecord(c->ev_used[k], c->stream));
     CUDA_TRY(cudaStreamWaitEvent(c->pre_stream, c->ev_used[k2], 0));
-    CUDA_TRY(launch_precompute(c->G, c->P, t0n, A.n_att, c->pre_stride, c->pre_buf[k2], c->pre_stream));
+    CUDA_TRY(launch_precompute(c->G, c->P, t0n, A.n_att, c->pre_stride, c->pre_buf[k2], c->n_sm, c->pre_stream));
     CUDA_TRY(cudaEventRecord(c->ev_pre[k2], c->pre_stream));
     c->pre_t0[k2] = t0n;
     c->pre_cur = k2;
@@ -541,12 +595,14 @@ rewl_status rewl_step(rewl_handle c, int64_t max_sweeps, int32_t* done) {
       swept += spe;
     }
     if (c->sweep_clock % (uint64_t)spf == 0) {
-      CUDA_TRY(d2h(c, c->h_n_done, c->S.n_done, sizeof(int32_t)));
+      CUDA_TRY(d2h(c, c->h_n_done, c->S.n_done, 2 * sizeof(int32_t)));
       CUDA_TRY(cudaStreamSynchronize(c->stream));
       if (c->ev_pending) {
         rewl_status st = collect_sweep_times(c);
         if (st != REWL_OK) return st;
       }
+      if (c->h_n_done[1] != 0)
+        return fail(REWL_ETIMEOUT, "a sweep kernel's bounded hand-off wait ran out (error bits %d)", c->h_n_done[1]);
       if (*c->h_n_done != c->n_done) {
         rewl_status st = upload_active(c);
         if (st != REWL_OK) return st;
@@ -597,6 +653,7 @@ rewl_status rewl_get_info(rewl_handle c, rewl_info* info) {
   info->h2d_bytes = (int64_t)c->h2d_bytes;
   info->d2h_bytes = (int64_t)c->d2h_bytes;
   info->prefetch_draws = c->pre_on ? 1 : 0;
+  info->sweep_variant = c->params.sweep_variant;
   return REWL_OK;
 }
 
@@ -611,6 +668,8 @@ rewl_status rewl_get_state(rewl_handle c, rewl_state* st) {
   if (st->lng) CUDA_TRY(d2h(c, st->lng, c->S.lng, 8 * nW * P.w));
   if (st->H) CUDA_TRY(d2h(c, st->H, c->S.H, 4 * nW * P.w));
   if (st->win_start) std::memcpy(st->win_start, c->win_start.data(), 4 * P.h);
+  if (st->win_width) std::memcpy(st->win_width, c->win_width.data(), 4 * P.h);
+  if (st->first_iter) CUDA_TRY(d2h(c, st->first_iter, c->S.first_iter, 8 * P.h));
   if (st->lnf) CUDA_TRY(d2h(c, st->lnf, c->S.lnf, 8 * P.h));
   if (st->iteration) CUDA_TRY(d2h(c, st->iteration, c->S.iter, 4 * P.h));
   if (st->done) CUDA_TRY(d2h(c, st->done, c->S.done, 4 * P.h));
@@ -639,7 +698,7 @@ rewl_status rewl_set_state(rewl_handle c, const rewl_state* st) {
     if (!is_pow2_double(st->lnf[a])) return fail(REWL_EINVAL, "lnf[%d] is not a power of two", a);
   for (size_t W = 0; W < nW; ++W) {
     const int a = (int)(W / P.m);
-    const int lo = P.e_min + c->win_start[a] * P.e_step, hi = lo + (P.w - 1) * P.e_step;
+    const int lo = P.e_min + c->win_start[a] * P.e_step, hi = lo + (c->win_width[a] - 1) * P.e_step;
     if (st->E[W] < lo || st->E[W] > hi || (st->E[W] - P.e_min) % P.e_step) return fail(REWL_EINVAL, "E[%zu] outside its window", W);
   }
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -650,6 +709,7 @@ rewl_status rewl_set_state(rewl_handle c, const rewl_state* st) {
   CUDA_TRY(h2d(c, c->S.lnf, st->lnf, 8 * P.h));
   CUDA_TRY(h2d(c, c->S.iter, st->iteration, 4 * P.h));
   CUDA_TRY(h2d(c, c->S.done, st->done, 4 * P.h));
+  if (st->first_iter) CUDA_TRY(h2d(c, c->S.first_iter, st->first_iter, 8 * P.h));
   if (st->stage) {
     for (int a = 0; a < P.h; ++a)
       if (st->stage[a] != 0 && (st->stage[a] != 1 || P.wl_rule != REWL_RULE_ONE_OVER_T))
@@ -708,7 +768,7 @@ rewl_status rewl_get_window_lng(rewl_handle c, int32_t window, int32_t walker, d
     std::memcpy(lng, means.data() + (size_t)window * P.w, 8 * (size_t)P.w);
   }
   if (bin_lo) *bin_lo = c->win_start[window];
-  if (n) *n = P.w;
+  if (n) *n = c->win_width[window];
   return REWL_OK;
 }
 
@@ -724,16 +784,16 @@ rewl_status rewl_get_lng(rewl_handle c, double* out, int32_t capacity, int32_t* 
   std::vector<double> M;
   rewl_status st = window_means(c, M);
   if (st != REWL_OK) return st;
-  const int w = P.w;
+  const int ld = P.w;  // row stride of the window means; window a has win_width[a] bins
   std::vector<double> g(P.n_bins, -INFINITY);
-  for (int b = 0; b < w; ++b)
+  for (int b = 0; b < c->win_width[0]; ++b)
     if (M[b] > 0.0) g[c->win_start[0] + b] = M[b];
   double shift_prev = 0.0;
   for (int a = 0; a + 1 < P.h; ++a) {
-    const double* A = &M[(size_t)a * w];
-    const double* B = &M[(size_t)(a + 1) * w];
+    const double* A = &M[(size_t)a * ld];
+    const double* B = &M[(size_t)(a + 1) * ld];
     const int sa = c->win_start[a], sb = c->win_start[a + 1];
-    const int lo = sb, hi = sa + w - 1;
+    const int lo = sb, hi = sa + c->win_width[a] - 1;
     int best_b = -1;
     double best = 0.0;
     for (int gb = lo + 1; gb < hi; ++gb) {
@@ -750,7 +810,7 @@ rewl_status rewl_get_lng(rewl_handle c, double* out, int32_t capacity, int32_t* 
         }
     if (best_b < 0) return fail(REWL_EINVAL, "windows %d and %d share no visited bin", a, a + 1);
     const double shift = (A[best_b - sa] + shift_prev) - B[best_b - sb];
-    for (int gb = best_b + 1; gb < sb + w; ++gb) {
+    for (int gb = best_b + 1; gb < sb + c->win_width[a + 1]; ++gb) {
       const double v = B[gb - sb];
       g[gb] = v > 0 ? v + shift : -INFINITY;
     }
@@ -768,6 +828,74 @@ rewl_status rewl_get_lng(rewl_handle c, double* out, int32_t capacity, int32_t* 
   if (n_bins) *n_bins = P.n_bins;
   if (e_min) *e_min = P.e_min;
   if (e_step) *e_step = P.e_step;
+  return REWL_OK;
+}
+
+
+// Run-time balanced partition (Fig. 1b and the speed-up paragraph: windows
+// sized so that every window finishes its first iteration after the same
+// number of sweeps, estimated from a pre-run with equal windows).  Reading:
+// the first iteration of a window is a diffusive walk whose duration is
+// (sum over its bins of rho(b))^2; pre-run window a (first merge after tau_a
+// sweeps, width w_a) gives rho_a = sqrt(tau_a) / w_a, and rho(b) is the mean
+// of rho_a over the pre-run windows containing b.  With U(b) = rho(0) + ... +
+// rho(b-1), the new windows are the equal partition of Fig. 1a laid out in U:
+// length lam = U(B) / (1 + (h-1)(1-o)), window k covers [u_k, u_k + lam],
+// u_k = k (U(B) - lam) / (h-1); it starts at the last bin b with U(b) <= u_k
+// and ends at the first bin b with U(b+1) >= u_k + lam (the first window at
+// bin 0, the last at bin B-1).
+rewl_status rewl_plan_windows(const int64_t* first_iter_sweeps, const int32_t* pre_starts, const int32_t* pre_widths,
+                              int32_t pre_windows, int32_t n_bins, int32_t windows, double overlap, int32_t* starts,
+                              int32_t* widths) {
+  if (!first_iter_sweeps || !pre_starts || !pre_widths || !starts || !widths || pre_windows < 1 || n_bins < 3 ||
+      windows < 1 || !(overlap > 0.0 && overlap < 1.0))
+    return fail(REWL_EINVAL, "rewl_plan_windows: invalid argument");
+  rewl_status st = check_windows(n_bins, pre_windows, pre_starts, pre_widths);
+  if (st != REWL_OK) return st;
+  std::vector<double> rho_w(pre_windows);
+  for (int a = 0; a < pre_windows; ++a) {
+    if (first_iter_sweeps[a] <= 0) return fail(REWL_EINVAL, "window %d has not finished its first iteration", a);
+    rho_w[a] = std::sqrt((double)first_iter_sweeps[a]) / (double)pre_widths[a];
+  }
+  std::vector<double> U(n_bins + 1, 0.0);
+  for (int b = 0; b < n_bins; ++b) {
+    double sum = 0.0;
+    int n = 0;
+    for (int a = 0; a < pre_windows; ++a)
+      if (pre_starts[a] <= b && b < pre_starts[a] + pre_widths[a]) {
+        sum = sum + rho_w[a];
+        ++n;
+      }
+    U[b + 1] = U[b] + sum / (double)n;
+  }
+  if (windows == 1) {
+    starts[0] = 0;
+    widths[0] = n_bins;
+    return REWL_OK;
+  }
+  const double T = U[n_bins];
+  const double lam = T / (1.0 + (double)(windows - 1) * (1.0 - overlap));
+  std::vector<int32_t> s0(windows), w0(windows);
+  for (int k = 0; k < windows; ++k) {
+    const double u_lo = ((double)k * (T - lam)) / (double)(windows - 1);
+    const double u_hi = u_lo + lam;
+    int first = 0, last = n_bins - 1;
+    if (k > 0)
+      for (int b = 0; b < n_bins; ++b)
+        if (U[b] <= u_lo) first = b;
+    if (k < windows - 1)
+      for (int b = 0; b < n_bins; ++b)
+        if (U[b + 1] >= u_hi) {
+          last = b;
+          break;
+        }
+    s0[k] = first;
+    w0[k] = last - first + 1;
+  }
+  st = check_windows(n_bins, windows, s0.data(), w0.data());
+  if (st != REWL_OK) return st;
+  std::memcpy(starts, s0.data(), sizeof(int32_t) * windows);
+  std::memcpy(widths, w0.data(), sizeof(int32_t) * windows);
   return REWL_OK;
 }
 

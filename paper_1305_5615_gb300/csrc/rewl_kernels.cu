@@ -8,6 +8,8 @@
 //                   f -> sqrt f and termination (paragraph after Eq. (1))
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdint>
 
 #include "rewl_device.cuh"
@@ -111,6 +113,13 @@ __global__ void k_init_lattice(Problem P, DevState S) {
 
 __device__ __forceinline__ int window_distance(int E, int lo, int hi) { return E < lo ? lo - E : (E > hi ? E - hi : 0); }
 
+// Bins of window a: its own width (run-time balanced windows of unequal width,
+// Fig. 1b), or P.w for every window when no table is given (Fig. 1a).  P.w is
+// always the largest width and the stride of the per-walker ln g and H rows.
+__device__ __forceinline__ int window_width(const Problem& P, const DevState& S, int a) {
+  return S.win_width ? S.win_width[a] : P.w;
+}
+
 // One greedy move on the entry stream.  target < 0: minimise E (descent);
 // otherwise minimise the distance to window `target`.
 __device__ void greedy_move(const Problem& P, DevState& S, uint32_t* lat, int W, int lo, int hi, bool descent) {
@@ -142,7 +151,7 @@ __global__ void k_entry(Problem P, DevState S, uint64_t budget) {
   uint32_t* lat = S.lat + (size_t)W * P.lat_words;
   const int a = W / P.m;
   const int lo = P.e_min + S.win_start[a] * P.e_step;
-  const int hi = P.e_min + (S.win_start[a] + P.w - 1) * P.e_step;
+  const int hi = P.e_min + (S.win_start[a] + window_width(P, S, a) - 1) * P.e_step;
   for (uint64_t n = 0; n < budget && window_distance(S.E[W], lo, hi) > 0; ++n) greedy_move(P, S, lat, W, lo, hi, false);
   if (window_distance(S.E[W], lo, hi) == 0) return;
   for (int i = 0; i < P.lat_words; ++i) lat[i] = S.seed_config[i];
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
     a = W / P.m;
     wstart = S.win_start[a];
     bin = (S.E[W] - P.e_min) / P.e_step - wstart;
-    if ((unsigned)bin >= (unsigned)P.w) {
+    if ((unsigned)bin >= (unsigned)window_width(P, S, a)) {
       if (lane == 0) S.status[W] = 6;
       valid = false;
     }
@@ -332,7 +341,7 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
     uint32_t h_cur = s_H[bin * wpb + lw];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
     const uint32_t gm = group_mask<G>();
-    const int L = P.L, w = P.w;
+    const int L = P.L, w = window_width(P, S, a);  // the window test; P.w is the layout stride
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
     StagedTrial* my_stage = s_stage + (size_t)lw * G;
 
@@ -507,15 +516,94 @@ __device__ __forceinline__ void apply_move_if(uint32_t* s_lat, uint32_t widx, ui
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised form (variant kSweepRing): a producer warp computes the
+// draws of upcoming groups (Philox, site, Potts offset, ln u, conflict mask)
+// into a ring of kRingSlots groups in shared memory while the walker's warp
+// runs the sequential chain; the walker's warp only evaluates the moves on the
+// current configuration.  The two warps sit on different SM sub-partitions,
+// so the producer does not take issue slots from the chain.  Hand-off through
+// mbarriers: full[s] (32 producer arrivals) and empty[s] (32 walker-warp
+// arrivals); every wait is bounded by a clock deadline, after which the warp
+// records an error (DevState.error) and leaves its loop.
+// ---------------------------------------------------------------------------
+constexpr int kRingSlots = 4;
+constexpr size_t kRingBytes = (size_t)kRingSlots * 32 * sizeof(PreTrial) + 2 * kRingSlots * sizeof(uint64_t);
+constexpr long long kRingWaitCycles = 1ll << 34;  // ~8 s at 2 GHz; a block takes milliseconds
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Whole warp: waits until every lane has seen the phase with the given parity
+// complete (each lane acquires for itself); false, for all lanes alike, once
+// lane 0's clock passes the deadline.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, long long deadline) {
+  const uint32_t a = smem_addr(bar);
+  bool ok = false;
+  while (true) {
+    if (!ok) ok = mbar_try_wait(a, parity);
+    if (__all_sync(0xffffffffu, ok)) return true;
+    if (__shfl_sync(0xffffffffu, clock64(), 0) > deadline) return false;
+  }
+}
+
+// The draw of trial t of walker W, with the conflict mask of its group of 32
+// (lane = t mod 32); the same values the in-kernel path computes.
+template <int MODEL>
+__device__ __forceinline__ PreTrial make_pretrial(const Problem& P, uint64_t t, int W, int lane) {
+  const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+  const uint32_t site = scale32(r.x, (uint32_t)P.N);
+  const int y = (int)mulhi32(site, P.magic_L);
+  const int x = (int)site - y * P.L;
+  const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+  const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
+  const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
+  const int L = P.L;
+  const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
+  const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
+  const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
+  const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
+  const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
+  uint32_t M = 0;
+#pragma unroll
+  for (int k = 0; k < 31; ++k) {
+    const uint32_t pi = __shfl_sync(0xffffffffu, pk, k);
+    const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
+    M |= (hit && k < lane) ? (1u << k) : 0u;
+  }
+  return PreTrial{pk | (pv << 16), M, thr};
+}
+
 // Runs the sweeps of the nloc walkers wids[0..nloc) of one CTA (wpb walkers per CTA).
-template <int MODEL, int G>
+// RING: warp-specialised form (G = 32, one walker, 64 threads: warp 0 the
+// walker, warp 1 the producer of its draws).
+template <int MODEL, int G, bool RING = false>
 __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevState& S, uint32_t n_att, int wpb,
                                                  const int32_t* wids, int nloc, const PreTrial* pre = nullptr,
                                                  uint32_t pre_stride = 0) {
   static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
+  static_assert(!RING || G == 32, "the ring form runs one walker on one warp");
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpad = P.w + 2 * kGuardBins;
-  StagedTrial* s_stage = reinterpret_cast<StagedTrial*>(smem);                 // [wpb][G]
+  PreTrial* s_ring = reinterpret_cast<PreTrial*>(smem);                                  // [kRingSlots][32]
+  uint64_t* s_full = reinterpret_cast<uint64_t*>(s_ring + kRingSlots * 32);              // [kRingSlots]
+  uint64_t* s_empty = s_full + kRingSlots;                                               // [kRingSlots]
+  StagedTrial* s_stage = reinterpret_cast<StagedTrial*>(smem + (RING ? kRingBytes : 0));  // [wpb][G]
   int64_t* s_fx = reinterpret_cast<int64_t*>(s_stage + (G > 1 ? (size_t)wpb * G : 0));  // [wpad][wpb]
   uint32_t* s_lat = reinterpret_cast<uint32_t*>(s_fx + (size_t)wpad * wpb);
   uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
@@ -534,17 +622,41 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   }
   if (MODEL == kEA)
     for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
+  if (RING && tid == 0)
+    for (int k = 0; k < kRingSlots; ++k) {
+      mbar_init(&s_full[k], 32);
+      mbar_init(&s_empty[k], 32);
+    }
   __syncthreads();
 
+  if (RING && tid >= 32) {  // ---- producer warp
+    if (nloc > 0) {
+      const int W = wids[0];
+      const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
+      const int lane = tid - 32;
+      const uint32_t n_groups = (n_att + 31) / 32;
+      const long long deadline = __shfl_sync(0xffffffffu, clock64(), 0) + kRingWaitCycles;
+      for (uint32_t g = 0; g < n_groups; ++g) {
+        const uint32_t sl = g % kRingSlots, rnd = g / kRingSlots;
+        if (rnd >= 1 && !mbar_wait_warp(&s_empty[sl], (rnd - 1) & 1u, deadline)) {
+          if (lane == 0) atomicOr(S.error, 1);
+          break;
+        }
+        s_ring[sl * 32 + lane] = make_pretrial<MODEL>(P, t0 + (uint64_t)g * 32 + lane, W, lane);
+        mbar_arrive(&s_full[sl]);
+      }
+    }
+  }
+
   const int lw = tid / G, lane = tid % G;
-  bool valid = lw < nloc;
+  bool valid = lw < nloc && !(RING && tid >= 32);
   int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
   if (valid) {
     W = wids[lw];
     a = W / P.m;
     wstart = S.win_start[a];
     bin = (S.E[W] - P.e_min) / P.e_step - wstart;
-    if ((unsigned)bin >= (unsigned)P.w) {
+    if ((unsigned)bin >= (unsigned)window_width(P, S, a)) {
       if (lane == 0) S.status[W] = 6;
       valid = false;
     }
@@ -556,19 +668,34 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     int64_t fx_cur = fxp[bin * wpb];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
     const uint32_t gm = group_mask<G>();
-    const int L = P.L, w = P.w;
+    const int L = P.L, w = window_width(P, S, a);  // the window test; P.w is the layout stride
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
     StagedTrial* my_stage = s_stage + (size_t)lw * G;
 
     const PreTrial* my_pre = pre ? pre + (size_t)W * pre_stride : nullptr;
     PreTrial nxt_pre{0u, 0u, 0};
     if (my_pre && (uint32_t)lane < n_att) nxt_pre = my_pre[lane];
+    long long deadline = 0;
+    if constexpr (RING) deadline = __shfl_sync(0xffffffffu, clock64(), 0) + kRingWaitCycles;
     for (uint32_t base = 0; base < n_att; base += G) {
       StagedTrial tr;
       {
         int x, y;
         uint32_t pv, M = 0;
-        if (my_pre) {  // draw prepared ahead by k_precompute; prefetch the next group's
+        if constexpr (RING) {  // draw from the producer warp's ring
+          const uint32_t g = base / 32, sl = g % kRingSlots;
+          if (!mbar_wait_warp(&s_full[sl], (g / kRingSlots) & 1u, deadline)) {
+            if (lane == 0) atomicOr(S.error, 2);
+            break;  // uniform over the warp: every lane waits on the same phase
+          }
+          const PreTrial pt = s_ring[sl * 32 + lane];
+          mbar_arrive(&s_empty[sl]);
+          x = (int)(pt.pk & 0xffu);
+          y = (int)((pt.pk >> 8) & 0xffu);
+          pv = pt.pk >> 16;
+          M = pt.mask;
+          tr.thr = pt.thr;
+        } else if (my_pre) {  // draw prepared ahead by k_precompute; prefetch the next group's
           const PreTrial pt = nxt_pre;
           if (base + G + (uint32_t)lane < n_att) nxt_pre = my_pre[base + G + lane];
           x = (int)(pt.pk & 0xffu);
@@ -745,50 +872,62 @@ __global__ void __launch_bounds__(256, 1) k_sweep_chain(Problem P, DevState S, S
                              A.pre_stride);
 }
 
+// One walker per CTA of 64 threads (G = 32): warp 0 the walker, warp 1 its draws.
+template <int MODEL>
+__global__ void __launch_bounds__(64, 1) k_sweep_ring(Problem P, DevState S, SweepLaunch A) {
+  sweep_chain_body<MODEL, 32, true>(P, S, A.n_att, 1, S.active + blockIdx.x, 1);
+}
+
 // ---------------------------------------------------------------------------
 // Draws of the next sweep launch, prepared while the current one runs (on the
 // SMs the walkers leave idle): for trial i of walker W the site, the proposed
 // Potts offset, ln u, and the conflict mask of its group of G trials -- the
 // same values the sweep kernel would compute, so the results are unchanged.
-// One thread per (walker, trial); trials are padded to a multiple of 32.
+// One thread per (walker, trial) in a grid-stride loop over a small grid (one
+// CTA per SM): a grid of thousands of CTAs that starts before the sweep
+// kernel's CTAs are placed would hold the SMs and pack the walkers' CTAs onto
+// few SMs when they free up.  Trials are padded to a multiple of 32, so every
+// warp is wholly in range or wholly out of it.
 // ---------------------------------------------------------------------------
 template <int G>
 __global__ void __launch_bounds__(256) k_precompute(Problem P, uint64_t t0, uint32_t n_att, uint32_t stride,
                                                     PreTrial* __restrict__ out) {
-  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int W = (int)(g / stride);
-  const uint32_t i = (uint32_t)(g - (uint64_t)W * stride);
-  if (W >= P.n_walkers) return;  // whole warps (stride is a multiple of 32)
-  const uint64_t t = t0 + i;
-  const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-  const uint32_t site = scale32(r.x, (uint32_t)P.N);
-  const int y = (int)mulhi32(site, P.magic_L);
-  const int x = (int)site - y * P.L;
-  const uint32_t pv = P.model == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
-  const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
-  const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
-  const int L = P.L;
-  const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
-  const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
-  const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
-  const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
-  const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
-  const int lane = (int)(i % G);
-  const uint32_t gm = group_mask<G>();
-  uint32_t M = 0;
+  const uint64_t total = (uint64_t)P.n_walkers * stride;
+  const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += step) {
+    const int W = (int)(g / stride);
+    const uint32_t i = (uint32_t)(g - (uint64_t)W * stride);
+    const uint64_t t = t0 + i;
+    const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+    const uint32_t site = scale32(r.x, (uint32_t)P.N);
+    const int y = (int)mulhi32(site, P.magic_L);
+    const int x = (int)site - y * P.L;
+    const uint32_t pv = P.model == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+    const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
+    const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
+    const int L = P.L;
+    const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
+    const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
+    const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
+    const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
+    const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
+    const int lane = (int)(i % G);
+    const uint32_t gm = group_mask<G>();
+    uint32_t M = 0;
 #pragma unroll
-  for (int k = 0; k < G - 1; ++k) {
-    const uint32_t pi = __shfl_sync(gm, pk, k, G);
-    const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
-    M |= (hit && k < lane) ? (1u << k) : 0u;
+    for (int k = 0; k < G - 1; ++k) {
+      const uint32_t pi = __shfl_sync(gm, pk, k, G);
+      const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
+      M |= (hit && k < lane) ? (1u << k) : 0u;
+    }
+    if (i < n_att) out[g] = PreTrial{pk | (pv << 16), M, thr};
   }
-  if (i < n_att) out[g] = PreTrial{pk | (pv << 16), M, thr};
 }
 
 cudaError_t launch_precompute(int G, const Problem& P, uint64_t t0, uint32_t n_att, uint32_t stride, PreTrial* out,
-                              cudaStream_t st) {
+                              int max_blocks, cudaStream_t st) {
   const uint64_t threads = (uint64_t)P.n_walkers * stride;
-  const unsigned blocks = (unsigned)((threads + 255) / 256);
+  const unsigned blocks = (unsigned)std::min<uint64_t>((threads + 255) / 256, (uint64_t)std::max(1, max_blocks));
   switch (G) {
     case 8: k_precompute<8><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
     case 16: k_precompute<16><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
@@ -821,8 +960,8 @@ __device__ __forceinline__ void exchange_body(const Problem& P, const DevState& 
     }
   }
   __syncthreads();
-  const int loA = P.e_min + S.win_start[a] * P.e_step, hiA = loA + (P.w - 1) * P.e_step;
-  const int loB = P.e_min + S.win_start[a + 1] * P.e_step, hiB = loB + (P.w - 1) * P.e_step;
+  const int loA = P.e_min + S.win_start[a] * P.e_step, hiA = loA + (window_width(P, S, a) - 1) * P.e_step;
+  const int loB = P.e_min + S.win_start[a + 1] * P.e_step, hiB = loB + (window_width(P, S, a + 1) - 1) * P.e_step;
   unsigned n_acc = 0;
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     const int Wi = a * m + k, Wj = (a + 1) * m + sigma[k];
@@ -871,7 +1010,7 @@ __device__ __forceinline__ void flat_merge_body(const Problem& P, const DevState
   __shared__ unsigned long long r_sum[32];
   __shared__ int r_n[32];
   __shared__ int all_flat;
-  const int m = P.m, w = P.w;
+  const int m = P.m, w = window_width(P, S, a), ld = P.w;  // window bins; row stride
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   // 1/t rule: ln f = 2^-k; t >= 2^(k+1) trials per level iff clock * N >= w * 2^(k+1)
   const int k = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
@@ -889,8 +1028,8 @@ __device__ __forceinline__ void flat_merge_body(const Problem& P, const DevState
       unsigned long long sum = 0;
       int n = 0;
       for (int b = threadIdx.x; b < w; b += blockDim.x) {
-        if (S.lng[(size_t)W * w + b] > 0.0) {
-          const uint32_t hv = S.H[(size_t)W * w + b];
+        if (S.lng[(size_t)W * ld + b] > 0.0) {
+          const uint32_t hv = S.H[(size_t)W * ld + b];
           hmin = min(hmin, hv);
           sum += hv;
           ++n;
@@ -929,15 +1068,16 @@ __device__ __forceinline__ void flat_merge_body(const Problem& P, const DevState
   }
   // merge: mean of the m estimators (summed in walker order), H reset
   for (int b = threadIdx.x; b < w; b += blockDim.x) {
-    double sum = S.lng[(size_t)(a * m) * w + b];
-    for (int kw = 1; kw < m; ++kw) sum = __dadd_rn(sum, S.lng[(size_t)(a * m + kw) * w + b]);
+    double sum = S.lng[(size_t)(a * m) * ld + b];
+    for (int kw = 1; kw < m; ++kw) sum = __dadd_rn(sum, S.lng[(size_t)(a * m + kw) * ld + b]);
     const double mean = __ddiv_rn(sum, (double)m);
     for (int kw = 0; kw < m; ++kw) {
-      S.lng[(size_t)(a * m + kw) * w + b] = mean;
-      S.H[(size_t)(a * m + kw) * w + b] = 0u;
+      S.lng[(size_t)(a * m + kw) * ld + b] = mean;
+      S.H[(size_t)(a * m + kw) * ld + b] = 0u;
     }
   }
   if (threadIdx.x == 0) {
+    if (S.iter[a] == 0 && S.first_iter) S.first_iter[a] = (int64_t)S.clock[0];  // end of the first iteration
     S.iter[a] += 1;
     if (P.wl_rule == 1 && stage == 0 && trials < next) {
       S.stage[a] = 1;  // halving would take ln f below 1/t: follow 1/t from here
@@ -1062,6 +1202,10 @@ template <int MODEL, int G>
 static cudaError_t prepare_sweep_t() {
   cudaError_t e = cudaFuncSetAttribute(k_sweep_spec<MODEL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e != cudaSuccess) return e;
+  if (G == 32) {
+    e = cudaFuncSetAttribute(k_sweep_ring<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(k_sweep_chain<MODEL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
@@ -1091,6 +1235,11 @@ cudaError_t prepare_sweep(int G, int model) {
 template <int MODEL, int G>
 static cudaError_t launch_sweep_t(const Problem& P, const DevState& S, const SweepLaunch& A, size_t smem,
                                   cudaStream_t st) {
+  if (A.variant == kSweepRing) {  // one walker per CTA: its warp and a producer warp
+    if (G != 32 || A.wpb != 1) return cudaErrorInvalidValue;
+    k_sweep_ring<MODEL><<<A.n_active, 64, smem, st>>>(P, S, A);
+    return cudaGetLastError();
+  }
   const int blocks = (A.n_active + A.wpb - 1) / A.wpb;
   sweep_kernel<MODEL, G>(A.variant)<<<blocks, A.wpb * G, smem, st>>>(P, S, A);
   return cudaGetLastError();
@@ -1115,6 +1264,7 @@ size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
                                      : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
   if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);
   if (P.model == kEA) b += (size_t)2 * P.L * P.Wr1 * 4;
+  if (variant == kSweepRing) b += kRingBytes;
   return b;
 }
 

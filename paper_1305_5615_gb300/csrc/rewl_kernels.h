@@ -14,7 +14,7 @@ cudaError_t prepare_sweep(int G, int model);
 cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const SweepLaunch& A, cudaStream_t st);
 cudaError_t launch_exchange(const Problem& P, const DevState& S, cudaStream_t st);
 cudaError_t launch_precompute(int G, const Problem& P, uint64_t t0, uint32_t n_att, uint32_t stride, PreTrial* out,
-                              cudaStream_t st);
+                              int max_blocks, cudaStream_t st);
 cudaError_t launch_advance_clock(const DevState& S, uint32_t sweeps, cudaStream_t st);
 cudaError_t launch_flat_merge(const Problem& P, const DevState& S, cudaStream_t st);
 cudaError_t launch_init(const Problem& P, const DevState& S, cudaStream_t st);

@@ -6,7 +6,8 @@
 //   lng   f64 [n_walkers][w]           ln g over the window's w bins
 //   H     u32 [n_walkers][w]           visit histogram of the iteration
 //   J     u32 [2][L][Wr1]              +-J couplings, bit 1 = J -1 (planes: right, down)
-//   win_start i32 [h], lnf f64 [h], iter i32 [h], done i32 [h], stage i32 [h]
+//   win_start i32 [h], win_width i32 [h] (P.w = the largest, the row stride of lng and H),
+//   lnf f64 [h], iter i32 [h], done i32 [h], stage i32 [h], first_iter i64 [h]
 //   counters u64: wl_accept / near_ties / exact_tests [n_walkers], x_tried / x_accepted [h]
 #pragma once
 #include <cstdint>
@@ -52,12 +53,16 @@ struct DevState {
   uint32_t* seed_config; // restart configuration for the entry walk
   uint64_t* clock;       // [0] sweeps done by the solve, [1] exchange rounds done, [2] trials (batched rounds)
   int32_t* stage;        // [h] 1/t rule: 0 = halving on the histogram test, 1 = following 1/t
+  int32_t* win_width;    // [h] bins of each window (NULL: P.w for all)
+  int64_t* first_iter;   // [h] sweep clock of each window's first merge, -1 before (may be NULL)
+  int32_t* error;        // one word: bits set by a sweep kernel whose bounded wait ran out (may be NULL)
 };
 
 // Sweep kernel variants (identical results): the staged form keeps H in
 // shared memory and runs a one-deep sequential chain; the chain form
-// speculates two deep and rebuilds H from the shadow.
-enum SweepVariant : int { kSweepChain = 0, kSweepStaged = 1 };
+// speculates two deep and rebuilds H from the shadow; the ring form is the
+// chain form with the draws made by a second, producer warp.
+enum SweepVariant : int { kSweepChain = 0, kSweepStaged = 1, kSweepRing = 2 };
 
 // A trial's draw, prepared ahead of its sweep launch by k_precompute: the
 // site (x | y << 8), the proposed Potts offset (<< 16), the mask of earlier

@@ -81,7 +81,7 @@ extern "C" rewl_status rewl_sweep_noalloc(const rewl_sweep_desc* d, uint32_t* la
   }
   const int L = d->L;
   const int64_t n_walkers = (int64_t)d->windows * d->walkers_per_window;
-  if (d->model < 0 || d->model > 2 || L < 2 || L > 128 || d->windows < 1 || d->walkers_per_window < 1 ||
+  if (d->model < 0 || d->model > 2 || L < 2 || L > 256 || d->windows < 1 || d->walkers_per_window < 1 ||
       d->window_bins < 3 || d->e_step < 1 || d->sweeps < 0 || (d->model == REWL_POTTS && (d->q < 2 || d->q > 16)) ||
       (d->model == REWL_EA_PM_J && !coupling_bits)) {
     rewl_set_last_error("rewl_sweep_noalloc: invalid descriptor");

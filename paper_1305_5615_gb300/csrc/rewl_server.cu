@@ -206,7 +206,7 @@ struct rewl_server {
       p.walkers_per_block = 1;
       p.mode = REWL_MODE_PLAIN;
       p.profile = 0;
-      p.prefetch_draws = -1;  // the batched kernels draw in-kernel
+      p.prefetch_draws = 0;  // the batched kernels draw in-kernel
       rewl_handle h = nullptr;
       const rewl_status st = rewl_create(&h, &r.model, &r.lattice, r.has_couplings ? r.couplings.data() : nullptr,
                                          r.windows, r.overlap, r.walkers_per_window, r.flatness, r.lnf_final, r.seed,
@@ -423,6 +423,8 @@ rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, in
   if (!out) return sfail(REWL_EINVAL, "NULL argument");
   if (device_bytes <= 0 || max_running < 1 || max_running > 65536)
     return sfail(REWL_EINVAL, "device_bytes must be > 0 and max_running in [1, 65536]");
+  if (params && (params->window_starts || params->window_widths))
+    return sfail(REWL_EINVAL, "a window table is per problem; served requests use the equal partition");
   rewl_server* s = new rewl_server();
   if (params) s->params = *params;
   else rewl_params_default(&s->params);
@@ -441,7 +443,7 @@ rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* q, uint
   if (!s || !q || !id) return sfail(REWL_EINVAL, "NULL argument");
   const int L = q->lattice.Lx;
   if (q->model.kind < 0 || q->model.kind > 2 || q->lattice.dim != 2 || q->lattice.Lx != q->lattice.Ly ||
-      q->lattice.periodic != 1 || L < 2 || L > 128 || q->windows < 1 || q->walkers_per_window < 1 ||
+      q->lattice.periodic != 1 || L < 2 || L > 256 || q->windows < 1 || q->walkers_per_window < 1 ||
       q->walkers_per_window > 4096 || !(q->overlap > 0.0 && q->overlap < 1.0))
     return sfail(REWL_EINVAL, "invalid request");
   if (q->model.kind != REWL_EA_PM_J && q->couplings) return sfail(REWL_EINVAL, "couplings are only taken by +-J");

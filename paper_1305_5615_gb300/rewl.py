@@ -27,7 +27,7 @@ EXPORTED = ["rewl_params_default", "rewl_create", "rewl_step", "rewl_get_lng", "
             "rewl_get_info", "rewl_get_state", "rewl_set_state", "rewl_destroy", "rewl_status_str",
             "rewl_last_error", "rewl_sweep_noalloc", "rewl_server_create", "rewl_server_submit", "rewl_server_run",
             "rewl_server_poll", "rewl_server_result", "rewl_server_cancel", "rewl_server_destroy", "rewl_thermo",
-            "rewl_thermo_jackknife"]
+            "rewl_thermo_jackknife", "rewl_plan_windows"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 
@@ -55,7 +55,8 @@ class rewl_params(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int64), ("stream", ctypes.c_void_p), ("lanes_per_walker", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("mode", ctypes.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("profile", ctypes.c_int32),
-                ("sweep_variant", ctypes.c_int32), ("prefetch_draws", ctypes.c_int32), ("wl_rule", ctypes.c_int32)]
+                ("sweep_variant", ctypes.c_int32), ("prefetch_draws", ctypes.c_int32), ("wl_rule", ctypes.c_int32),
+                ("window_starts", ctypes.c_void_p), ("window_widths", ctypes.c_void_p)]
 
 
 class rewl_info(ctypes.Structure):
@@ -64,7 +65,7 @@ class rewl_info(ctypes.Structure):
                  "e_step", "lattice_words", "lanes_per_walker", "walkers_per_block", "mode", "windows_done")] + \
                [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
-                ("d2h_bytes", ctypes.c_int64), ("prefetch_draws", ctypes.c_int32)]
+                ("d2h_bytes", ctypes.c_int64), ("prefetch_draws", ctypes.c_int32), ("sweep_variant", ctypes.c_int32)]
 
 
 class rewl_sweep_desc(ctypes.Structure):
@@ -96,7 +97,8 @@ class rewl_state(ctypes.Structure):
     _fields_ = [(n, ctypes.c_void_p) for n in
                 ("lattice", "E", "lng", "H", "win_start", "lnf", "iteration", "done", "wl_accept", "near_ties",
                  "exact_tests", "x_tried", "x_accepted")] + \
-               [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("stage", ctypes.c_void_p)]
+               [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("stage", ctypes.c_void_p),
+                ("win_width", ctypes.c_void_p), ("first_iter", ctypes.c_void_p)]
 
 
 _lib = None
@@ -164,6 +166,8 @@ def load(build_if_missing=True):
     L.rewl_thermo_jackknife.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
                                         ctypes.c_int32, P, P]
     L.rewl_thermo_jackknife.restype = ctypes.c_int
+    L.rewl_plan_windows.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, P]
+    L.rewl_plan_windows.restype = ctypes.c_int
     L.rewl_thermo.restype = ctypes.c_int
     _lib = L
     return L
@@ -232,7 +236,8 @@ def rewl_get_state(h, info):
          "win_start": np.zeros(hw, np.int32), "lnf": np.zeros(hw, np.float64), "iteration": np.zeros(hw, np.int32),
          "done": np.zeros(hw, np.int32), "wl_accept": np.zeros(nW, np.uint64), "near_ties": np.zeros(nW, np.uint64),
          "exact_tests": np.zeros(nW, np.uint64), "x_tried": np.zeros(hw, np.uint64),
-         "x_accepted": np.zeros(hw, np.uint64), "stage": np.zeros(hw, np.int32)}
+         "x_accepted": np.zeros(hw, np.uint64), "stage": np.zeros(hw, np.int32), "win_width": np.zeros(hw, np.int32),
+         "first_iter": np.zeros(hw, np.int64)}
     s = rewl_state(**{k: _p(v) for k, v in a.items()})
     _check(load().rewl_get_state(h, ctypes.byref(s)), "rewl_get_state")
     a["sweep_clock"], a["exchange_rounds"] = s.sweep_clock, s.exchange_rounds
@@ -240,7 +245,7 @@ def rewl_get_state(h, info):
 
 
 def rewl_set_state(h, state):
-    keys = [k for k, _ in rewl_state._fields_ if k not in ("sweep_clock", "exchange_rounds")]
+    keys = [k for k, _ in rewl_state._fields_ if k not in ("sweep_clock", "exchange_rounds", "win_width")]
     arrs = {k: (np.ascontiguousarray(state[k]) if state.get(k) is not None else None) for k in keys}
     s = rewl_state(**{k: _p(v) for k, v in arrs.items()})
     s.sweep_clock, s.exchange_rounds = int(state["sweep_clock"]), int(state["exchange_rounds"])
@@ -265,6 +270,18 @@ def rewl_thermo(lng, e_min, e_step, temperatures):
     out = np.zeros((len(T), 5), np.float64)
     _check(load().rewl_thermo(_p(g), len(g), e_min, e_step, _p(T), len(T), _p(out)), "rewl_thermo")
     return out
+
+
+def rewl_plan_windows(first_iter_sweeps, pre_starts, pre_widths, n_bins, windows, overlap):
+    """Run-time balanced partition (Fig. 1b) from a pre-run: (starts, widths)."""
+    f = np.ascontiguousarray(first_iter_sweeps, dtype=np.int64)
+    ps = np.ascontiguousarray(pre_starts, dtype=np.int32)
+    pw = np.ascontiguousarray(pre_widths, dtype=np.int32)
+    st = np.zeros(windows, np.int32)
+    wd = np.zeros(windows, np.int32)
+    _check(load().rewl_plan_windows(_p(f), _p(ps), _p(pw), len(ps), int(n_bins), int(windows), float(overlap), _p(st),
+                                    _p(wd)), "rewl_plan_windows")
+    return st, wd
 
 
 def rewl_thermo_jackknife(lng_runs, e_min, e_step, temperatures):
@@ -310,7 +327,7 @@ class REWL:
                  couplings=None, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
                  entry_max_sweeps=1000, discovery_sweeps=200, timeout_ms=0, lanes_per_walker=0,
                  walkers_per_block=0, mode=MODE_PLAIN, stream=None, torch_allocator=False, profile=False,
-                 sweep_variant=0, prefetch_draws=0, wl_rule=0):
+                 sweep_variant=-1, prefetch_draws=0, wl_rule=0, window_starts=None, window_widths=None):
         if isinstance(model, str):
             model = MODELS[model]
         p = rewl_params_default()
@@ -321,6 +338,10 @@ class REWL:
         p.sweep_variant = sweep_variant
         p.prefetch_draws = prefetch_draws
         p.wl_rule = WL_RULES[wl_rule] if isinstance(wl_rule, str) else wl_rule
+        if window_starts is not None:
+            self._win = (np.ascontiguousarray(window_starts, dtype=np.int32),
+                         np.ascontiguousarray(window_widths, dtype=np.int32))
+            p.window_starts, p.window_widths = self._win[0].ctypes.data, self._win[1].ctypes.data
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._keep = None

@@ -7,14 +7,16 @@ from paper_1305_5615_gb300 import rewl
 
 
 def make_pair(model, L, h, o, m, flatness, lnf_final, seed, q=2, couplings=None, spe=100, spf=1000, lnf0=1.0,
-              G=0, wpb=0, mode=rewl.MODE_PLAIN, entry_max_sweeps=1000, discovery_sweeps=200, wl_rule="flat"):
+              G=0, wpb=0, mode=rewl.MODE_PLAIN, entry_max_sweeps=1000, discovery_sweeps=200, wl_rule="flat",
+              window_starts=None, window_widths=None):
     O = OracleREWL(model, L, h, o, m, flatness, lnf_final, seed, q=q, couplings=couplings, sweeps_per_exchange=spe,
                    sweeps_per_flat_check=spf, lnf0=lnf0, entry_max_sweeps=entry_max_sweeps,
-                   discovery_sweeps=discovery_sweeps, wl_rule=wl_rule)
+                   discovery_sweeps=discovery_sweeps, wl_rule=wl_rule, window_starts=window_starts,
+                   window_widths=window_widths)
     D = rewl.REWL(model, L, h, o, m, flatness, lnf_final, seed, q=q, couplings=couplings, sweeps_per_exchange=spe,
                   sweeps_per_flat_check=spf, lnf0=lnf0, entry_max_sweeps=entry_max_sweeps,
                   discovery_sweeps=discovery_sweeps, lanes_per_walker=G, walkers_per_block=wpb, mode=mode,
-                  wl_rule=wl_rule)
+                  wl_rule=wl_rule, window_starts=window_starts, window_widths=window_widths)
     return O, D
 
 
@@ -32,6 +34,8 @@ def compare_states(O, D, where=""):
     spins = rewl.unpack_lattice(sg["lattice"], D.info["L"], model)
     assert D.info["window_bins"] == O.w and D.info["n_bins"] == O.n_bins and D.info["e_min"] == O.e_min, where
     assert np.array_equal(sg["win_start"], wo["start"]), where
+    assert np.array_equal(sg["win_width"], wo["width"]), where
+    assert np.array_equal(sg["first_iter"], wo["first_iter"]), where
     bad = np.nonzero((spins != so["spins"]).any(1))[0]
     assert bad.size == 0, "%s: configurations differ for walkers %s" % (where, bad[:8])
     assert np.array_equal(sg["E"], so["E"]), where

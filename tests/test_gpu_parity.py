@@ -178,6 +178,36 @@ def test_torch_allocator_and_stream():
     assert torch.cuda.memory_allocated() == before
 
 
+# ------------------------------------------ the warp-specialised ring variant
+@pytest.mark.parametrize("model,L,q,h,m", [("ising", 8, 2, 4, 2), ("ising", 5, 2, 3, 2), ("potts", 8, 10, 4, 2),
+                                           ("ea", 8, 2, 4, 2), ("ising", 32, 2, 16, 4)])
+def test_ring_variant_matches_oracle(model, L, q, h, m):
+    """sweep_variant 2: draws from a producer warp through a shared-memory ring
+    (L=5: 2500 trials per launch, a ragged last group of 4)."""
+    O = OracleREWL(model, L, h, 0.75, m, 0.8, 1e-6, 71 + L, q=q)
+    D = rewl.REWL(model, L, h, 0.75, m, 0.8, 1e-6, 71 + L, q=q, sweep_variant=2)
+    assert (D.info["lanes_per_walker"], D.info["walkers_per_block"], D.info["sweep_variant"]) == (32, 1, 2)
+    _parity(O, D, [1, 12], "ring %s L=%d" % (model, L))
+
+
+def test_ring_variant_full_run_and_served_shapes():
+    O, _ = make_pair("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0)
+    D = rewl.REWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, sweep_variant=2)
+    for _ in range(10000):
+        done_o, done_d = run_both(O, D, 10)
+        assert compare_states(O, D, "ring full run") == 0
+        assert done_o == done_d
+        if done_o:
+            break
+    assert done_o
+    with pytest.raises(rewl.RewlError):
+        rewl.REWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, sweep_variant=2, lanes_per_walker=8)
+    # the automatic choice: the ring form for few walkers, the chain form for many or forced lanes
+    assert rewl.REWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0).info["sweep_variant"] == 2
+    assert rewl.REWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, lanes_per_walker=8).info["sweep_variant"] == 0
+    assert rewl.REWL("potts", 16, 32, 0.75, 64, 0.8, 1e-6, 0, q=3).info["sweep_variant"] == 0
+
+
 # ------------------------------------------------- the staged sweep variant
 @pytest.mark.parametrize("model,L,q,G", [("ising", 8, 2, 32), ("ising", 12, 2, 8), ("potts", 8, 10, 32), ("ea", 8, 2, 16)])
 def test_staged_variant_matches_oracle(model, L, q, G):
@@ -242,8 +272,9 @@ def test_prefetched_draws_match_in_kernel_draws_and_the_oracle():
     on a second stream the states equal those of the in-kernel draws and of the
     oracle; a rewind through rewl_set_state (stale prepared buffers) and a
     replay give the same bits again."""
-    O, A = make_pair("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5)
-    B = rewl.REWL("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5, prefetch_draws=-1)
+    O = OracleREWL("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5)
+    A = rewl.REWL("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5, prefetch_draws=1, sweep_variant=0)
+    B = rewl.REWL("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 5, prefetch_draws=0, sweep_variant=0)
     assert A.info["prefetch_draws"] == 1 and B.info["prefetch_draws"] == 0
     A.step(1000)
     B.step(1000)
