@@ -26,8 +26,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-ISING, POTTS, EA = 0, 1, 2
-MODEL_NAMES = {"ising": ISING, "potts": POTTS, "ea": EA}
+ISING, POTTS, EA, EA3 = 0, 1, 2, 3
+MODEL_NAMES = {"ising": ISING, "potts": POTTS, "ea": EA, "ea3d": EA3}
 WL_RULES = {"flat": 0, "1/t": 1}
 
 
@@ -177,7 +177,7 @@ class OracleREWL:
         return {"spins": spins, "E": E, "lng": lng, "H": H}
 
     def couplings(self):
-        J = np.zeros(2 * self.N, np.int8)
+        J = np.zeros((3 if self.model == EA3 else 2) * self.N, np.int8)
         self._lib.orc_get_couplings(self._h, _ptr(J))
         return J
 

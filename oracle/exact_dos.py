@@ -34,9 +34,34 @@ def _bonds(L):
     return right, down
 
 
+def _bonds3(L):
+    """Right, down and behind neighbours on the periodic L x L x L cube, site
+    i = (z L + y) L + x."""
+    N = L ** 3
+    i = np.arange(N)
+    x, y, z = i % L, (i // L) % L, i // (L * L)
+    at = lambda a, b, c: (c * L + b) * L + a
+    return at((x + 1) % L, y, z), at(x, (y + 1) % L, z), at(x, y, (z + 1) % L)
+
+
 def enumerate_dos(L, model="ising", q=2, couplings=None):
     """Brute force over all configurations.  couplings: 2N values +-1 (right,
-    down of each site) for the +-J model."""
+    down of each site) for the +-J model, 3N (right, down, behind) for the
+    3D +-J model "ea3d" on the L x L x L cube."""
+    if model == "ea3d":
+        N = L ** 3
+        if N > 20:
+            raise ValueError("too many configurations")
+        nb = _bonds3(L)
+        c = np.ones((N, 3), np.int64) if couplings is None else np.asarray(couplings, np.int64).reshape(N, 3)
+        idx = np.arange(1 << N, dtype=np.int64)
+        spin = lambda i: 1 - 2 * ((idx >> i) & 1)
+        E = np.zeros(1 << N, np.int64)
+        for i in range(N):
+            for d in range(3):
+                E -= c[i, d] * spin(i) * spin(int(nb[d][i]))
+        vals, counts = np.unique(E, return_counts=True)
+        return [int(v) for v in vals], [int(c) for c in counts]
     N = L * L
     right, down = _bonds(L)
     if model == "potts":

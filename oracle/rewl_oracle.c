@@ -89,10 +89,14 @@ static double uniform_open01(uint32_t r2, uint32_t r3) {
 /* ------------------------------------------------------------------------ */
 /* Model: energy and its change under a single-site move.                  */
 /* ------------------------------------------------------------------------ */
-static int right_of(const orc_rewl* R, int i) { int x = i % R->L, y = i / R->L; return y * R->L + (x + 1) % R->L; }
-static int left_of(const orc_rewl* R, int i) { int x = i % R->L, y = i / R->L; return y * R->L + (x + R->L - 1) % R->L; }
-static int down_of(const orc_rewl* R, int i) { int x = i % R->L, y = i / R->L; return ((y + 1) % R->L) * R->L + x; }
-static int up_of(const orc_rewl* R, int i) { int x = i % R->L, y = i / R->L; return ((y + R->L - 1) % R->L) * R->L + x; }
+/* Site i = (z L + y) L + x (z = 0 in 2D); neighbours on the periodic lattice. */
+static int site_at(const orc_rewl* R, int x, int y, int z) { return (z * R->L + y) * R->L + x; }
+static int right_of(const orc_rewl* R, int i) { int L = R->L, x = i % L, y = (i / L) % L, z = i / (L * L); return site_at(R, (x + 1) % L, y, z); }
+static int left_of(const orc_rewl* R, int i) { int L = R->L, x = i % L, y = (i / L) % L, z = i / (L * L); return site_at(R, (x + L - 1) % L, y, z); }
+static int down_of(const orc_rewl* R, int i) { int L = R->L, x = i % L, y = (i / L) % L, z = i / (L * L); return site_at(R, x, (y + 1) % L, z); }
+static int up_of(const orc_rewl* R, int i) { int L = R->L, x = i % L, y = (i / L) % L, z = i / (L * L); return site_at(R, x, (y + L - 1) % L, z); }
+static int back_of(const orc_rewl* R, int i) { int L = R->L, x = i % L, y = (i / L) % L, z = i / (L * L); return site_at(R, x, y, (z + 1) % L); }
+static int front_of(const orc_rewl* R, int i) { int L = R->L, x = i % L, y = (i / L) % L, z = i / (L * L); return site_at(R, x, y, (z + L - 1) % L); }
 
 static int ising_s(uint8_t b) { return 1 - 2 * (int)b; }
 
@@ -103,23 +107,30 @@ static int bond_energy(const orc_rewl* R, int J, uint8_t a, uint8_t b) {
   return -J * ising_s(a) * ising_s(b);
 }
 
-/* Full energy E = sum over the 2N bonds (right and down of every site). */
+/* Full energy E = sum over the dim N bonds (right, down and, in 3D, behind
+ * every site). */
 int orc_energy(const orc_rewl* R, const uint8_t* s) {
   int E = 0;
   for (int i = 0; i < R->N; ++i) {
     E += bond_energy(R, R->Jr[i], s[i], s[right_of(R, i)]);
     E += bond_energy(R, R->Jd[i], s[i], s[down_of(R, i)]);
+    if (R->dim == 3) E += bond_energy(R, R->Jb[i], s[i], s[back_of(R, i)]);
   }
   return E;
 }
 
-/* Energy change when site i takes value v_new: the four bonds at i. */
+/* Energy change when site i takes value v_new: the 2 dim bonds at i. */
 static int delta_energy(const orc_rewl* R, const uint8_t* s, int i, uint8_t v_new) {
   int r = right_of(R, i), l = left_of(R, i), d = down_of(R, i), u = up_of(R, i);
   int before = bond_energy(R, R->Jr[i], s[i], s[r]) + bond_energy(R, R->Jr[l], s[l], s[i]) +
                bond_energy(R, R->Jd[i], s[i], s[d]) + bond_energy(R, R->Jd[u], s[u], s[i]);
   int after = bond_energy(R, R->Jr[i], v_new, s[r]) + bond_energy(R, R->Jr[l], s[l], v_new) +
               bond_energy(R, R->Jd[i], v_new, s[d]) + bond_energy(R, R->Jd[u], s[u], v_new);
+  if (R->dim == 3) {
+    int b = back_of(R, i), f = front_of(R, i);
+    before += bond_energy(R, R->Jb[i], s[i], s[b]) + bond_energy(R, R->Jb[f], s[f], s[i]);
+    after += bond_energy(R, R->Jb[i], v_new, s[b]) + bond_energy(R, R->Jb[f], s[f], v_new);
+  }
   return after - before;
 }
 
@@ -146,7 +157,7 @@ static int bin_of(const orc_rewl* R, int E) { return (E - R->e_min) / R->e_step;
  * A partition given explicitly (Fig. 1b: run-time balanced windows of
  * unequal width) must start at bin 0, end at bin B-1, have widths >= 3,
  * strictly increasing starts and ends, and neighbours sharing >= 1 bin. */
-static int make_windows(orc_rewl* R) {
+static int make_windows(orc_rewl* R, int core_lo, int core_bins) {
   int B = R->n_bins, h = R->h;
   if (R->params.window_starts) {
     const int32_t* st = R->params.window_starts;
@@ -169,18 +180,26 @@ static int make_windows(orc_rewl* R) {
     R->win_width[0] = B;
     return ORC_OK;
   }
-  double wd = ceil((double)B / (1.0 + (double)(h - 1) * (1.0 - R->overlap)));
+  /* the equal partition of the core [core_lo, core_lo + core_bins); the first
+   * and the last window then reach down to bin 0 and up to bin B-1 */
+  int Bc = core_bins;
+  double wd = ceil((double)Bc / (1.0 + (double)(h - 1) * (1.0 - R->overlap)));
   int w = (int)wd;
-  if (w > B) w = B;
+  if (w > Bc) w = Bc;
   if (w < 3) return ORC_EINVAL;
-  R->w = w;
   for (int k = 0; k < h; ++k) {
-    int64_t num = 2 * (int64_t)k * (int64_t)(B - w) + (h - 1);
-    R->win_start[k] = (int)(num / (2 * (int64_t)(h - 1)));
+    int64_t num = 2 * (int64_t)k * (int64_t)(Bc - w) + (h - 1);
+    R->win_start[k] = core_lo + (int)(num / (2 * (int64_t)(h - 1)));
     R->win_width[k] = w;
   }
   for (int k = 0; k + 1 < h; ++k)
     if (R->win_start[k + 1] > R->win_start[k] + w - 1) return ORC_EINVAL; /* neighbours must overlap */
+  R->win_width[0] += R->win_start[0];
+  R->win_start[0] = 0;
+  R->win_width[h - 1] = B - R->win_start[h - 1];
+  R->w = 0;
+  for (int k = 0; k < h; ++k)
+    if (R->win_width[k] > R->w) R->w = R->win_width[k];
   return ORC_OK;
 }
 
@@ -271,45 +290,50 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   *out = NULL;
   orc_params P;
   if (params) P = *params; else orc_default_params(&P);
-  if (model < 0 || model > 2 || L < 2 || L > 256 || h < 1 || m < 1 || h * m > (1 << 20)) return ORC_EINVAL;
+  if (model < 0 || model > 3 || L < 2 || L > 256 || h < 1 || m < 1 || h * m > (1 << 20)) return ORC_EINVAL;
   if (model == ORC_POTTS && (q < 2 || q > 16)) return ORC_EINVAL;
-  if (model == ORC_EA && (L % 2) != 0) return ORC_EINVAL;
+  if ((model == ORC_EA || model == ORC_EA3) && (L % 2) != 0) return ORC_EINVAL;
+  if (model == ORC_EA3 && L > 64) return ORC_EINVAL;
   if (!(overlap > 0.0 && overlap < 1.0) || !(flatness > 0.0 && flatness <= 1.0) || !(lnf_final > 0.0)) return ORC_EINVAL;
   if (!(P.lnf0 >= lnf_final) || P.sweeps_per_exchange < 1 || P.sweeps_per_flat_check < P.sweeps_per_exchange ||
       P.sweeps_per_flat_check % P.sweeps_per_exchange != 0 || P.entry_max_sweeps < 1 || P.discovery_sweeps < 0 ||
       (P.wl_rule != 0 && P.wl_rule != 1))
     return ORC_EINVAL;
-  if (model != ORC_EA && couplings != NULL) return ORC_EINVAL;
+  if (model != ORC_EA && model != ORC_EA3 && couplings != NULL) return ORC_EINVAL;
 
   orc_rewl* R = (orc_rewl*)calloc(1, sizeof(orc_rewl));
-  R->model = model; R->q = (model == ORC_POTTS) ? q : 2; R->L = L; R->N = L * L;
+  R->model = model; R->q = (model == ORC_POTTS) ? q : 2; R->L = L;
+  R->dim = model == ORC_EA3 ? 3 : 2;
+  R->N = R->dim == 3 ? L * L * L : L * L;
   R->h = h; R->m = m; R->overlap = overlap; R->flatness = flatness; R->lnf_final = lnf_final; R->seed = seed;
   R->params = P;
   int N = R->N, n_walkers = h * m;
   R->Jr = (int8_t*)malloc((size_t)N);
   R->Jd = (int8_t*)malloc((size_t)N);
-  /* couplings: Ising and Potts J = 1; +-J either given (2N values, right then
-   * down of every site) or drawn with p = 1/2 from the request seed. */
-  int n_negative = 0;
+  R->Jb = (int8_t*)malloc((size_t)N);
+  /* couplings: Ising and Potts J = 1; +-J either given (dim N values: right,
+   * down and, in 3D, behind of every site) or drawn with p = 1/2 from the
+   * request seed (bond b = dim i + d is bit b of the coupling stream). */
+  int n_negative = 0, D = R->dim;
   for (int i = 0; i < N; ++i) {
-    int jr = 1, jd = 1;
-    if (model == ORC_EA) {
-      if (couplings) {
-        jr = couplings[2 * i];
-        jd = couplings[2 * i + 1];
-        if ((jr != 1 && jr != -1) || (jd != 1 && jd != -1)) { orc_destroy(R); return ORC_EINVAL; }
-      } else {
-        uint32_t r[4];
-        int b0 = 2 * i, b1 = 2 * i + 1;
-        draw(R, (uint32_t)(b0 / 128), 0, 0xFFFFFFFFu, TAG_COUPLING, r);
-        jr = ((r[(b0 % 128) / 32] >> (b0 % 32)) & 1u) ? -1 : 1;
-        draw(R, (uint32_t)(b1 / 128), 0, 0xFFFFFFFFu, TAG_COUPLING, r);
-        jd = ((r[(b1 % 128) / 32] >> (b1 % 32)) & 1u) ? -1 : 1;
+    int j[3] = {1, 1, 1};
+    if (model == ORC_EA || model == ORC_EA3) {
+      for (int d = 0; d < D; ++d) {
+        if (couplings) {
+          j[d] = couplings[D * i + d];
+          if (j[d] != 1 && j[d] != -1) { orc_destroy(R); return ORC_EINVAL; }
+        } else {
+          uint32_t r[4];
+          int b = D * i + d;
+          draw(R, (uint32_t)(b / 128), 0, 0xFFFFFFFFu, TAG_COUPLING, r);
+          j[d] = ((r[(b % 128) / 32] >> (b % 32)) & 1u) ? -1 : 1;
+        }
       }
     }
-    R->Jr[i] = (int8_t)jr;
-    R->Jd[i] = (int8_t)jd;
-    n_negative += (jr < 0) + (jd < 0);
+    R->Jr[i] = (int8_t)j[0];
+    R->Jd[i] = (int8_t)j[1];
+    R->Jb[i] = (int8_t)j[2];
+    n_negative += (j[0] < 0) + (j[1] < 0) + (D == 3 && j[2] < 0);
   }
   R->spins = (uint8_t*)calloc((size_t)n_walkers * N, 1);
   R->E = (int*)calloc((size_t)n_walkers, sizeof(int));
@@ -334,10 +358,15 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   }
 
   /* Energy range.  Ising: [-2N, 2N] in steps of 4.  Potts: [-2N, 0] in
-   * steps of 1.  +-J: steps of 4 with E = -2N + 2 n_neg (mod 4); the lower
-   * end is found by a zero-temperature descent of every walker (the lowest
-   * energy any walker reaches), the upper end is its mirror image, using
-   * g(E) = g(-E) on the bipartite periodic lattice (flip one sublattice). */
+   * steps of 1.  +-J (2D and 3D): steps of 4 with E = -dim N + 2 n_neg
+   * (mod 4).  A zero-temperature descent of every walker finds E_d (the
+   * lowest energy any walker reaches); the windows are laid out over the
+   * core [E_d, -E_d] (g(E) = g(-E) on the bipartite periodic lattice: flip
+   * one sublattice), and the lowest and highest windows reach on to the
+   * bounds of the grid, e_min = E_d - 4 floor((E_d + dim N) / 4) >= -dim N and
+   * e_max = -e_min, so the walk can still find energies below E_d (no energy
+   * is locked out; bins never visited stay out of the flatness test). */
+  int core_lo = 0, core_bins = 0;
   if (model == ORC_ISING) {
     R->e_min = -2 * N; R->e_max = 2 * N; R->e_step = 4;
   } else if (model == ORC_POTTS) {
@@ -352,13 +381,16 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
     }
     (void)n_negative;
     if (best >= 0) { orc_destroy(R); return ORC_EENTRY; }
-    R->e_min = best; R->e_max = -best;
+    core_lo = (best + R->dim * N) / 4;
+    R->e_min = best - 4 * core_lo; R->e_max = -R->e_min;
+    core_bins = (-2 * best) / 4 + 1;
     memcpy(R->seed_config, spins_of(R, best_W), (size_t)N);
   }
   R->n_bins = (R->e_max - R->e_min) / R->e_step + 1;
-  if (make_windows(R) != ORC_OK) { orc_destroy(R); return ORC_EINVAL; }
+  if (core_bins == 0) core_bins = R->n_bins;
+  if (make_windows(R, core_lo, core_bins) != ORC_OK) { orc_destroy(R); return ORC_EINVAL; }
   /* Ising / Potts restart configuration: the ground state (all b = 0). */
-  if (model != ORC_EA) memset(R->seed_config, 0, (size_t)N);
+  if (model != ORC_EA && model != ORC_EA3) memset(R->seed_config, 0, (size_t)N);
 
   R->lng = (double*)calloc((size_t)n_walkers * R->w, sizeof(double));
   R->H = (uint32_t*)calloc((size_t)n_walkers * R->w, sizeof(uint32_t));
@@ -374,7 +406,7 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
 
 void orc_destroy(orc_rewl* R) {
   if (!R) return;
-  free(R->Jr); free(R->Jd); free(R->spins); free(R->E); free(R->entry_t); free(R->seed_config);
+  free(R->Jr); free(R->Jd); free(R->Jb); free(R->spins); free(R->E); free(R->entry_t); free(R->seed_config);
   free(R->win_start); free(R->win_width); free(R->first_iter); free(R->lnf); free(R->iter); free(R->done); free(R->phase); free(R->lng); free(R->H);
   free(R->wl_accept); free(R->near_ties); free(R->x_tried); free(R->x_accepted);
   free(R);
@@ -657,7 +689,11 @@ void orc_get_walkers(const orc_rewl* R, uint8_t* spins, int32_t* E, double* lng,
 }
 
 void orc_get_couplings(const orc_rewl* R, int8_t* J) {
-  for (int i = 0; i < R->N; ++i) { J[2 * i] = R->Jr[i]; J[2 * i + 1] = R->Jd[i]; }
+  for (int i = 0; i < R->N; ++i) {
+    J[R->dim * i] = R->Jr[i];
+    J[R->dim * i + 1] = R->Jd[i];
+    if (R->dim == 3) J[3 * i + 2] = R->Jb[i];
+  }
 }
 
 void orc_get_counters(const orc_rewl* R, uint64_t* wl_accept, uint64_t* near_ties, uint64_t* x_tried,

@@ -7,7 +7,7 @@
 #define REWL_ORACLE_H
 #include <stdint.h>
 
-enum { ORC_ISING = 0, ORC_POTTS = 1, ORC_EA = 2 };
+enum { ORC_ISING = 0, ORC_POTTS = 1, ORC_EA = 2, ORC_EA3 = 3 };  /* ORC_EA3: +-J on the L x L x L cube */
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_EENTRY = 5 };
 
 typedef struct {
@@ -23,7 +23,8 @@ typedef struct {
 
 typedef struct orc_rewl {
   int model, q, L, N;
-  int8_t *Jr, *Jd;            /* couplings of the bond to the right / below each site */
+  int dim;                    /* 2, or 3 for ORC_EA3 (N = L^3, site i = (z L + y) L + x) */
+  int8_t *Jr, *Jd, *Jb;       /* couplings of the bond to the right / below / behind (3D) each site */
   int e_min, e_max, e_step, n_bins;
   int h, m, w;
   double overlap, flatness, lnf_final;

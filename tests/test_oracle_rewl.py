@@ -206,7 +206,8 @@ def test_converges_ea_L4_given_couplings():
     J = np.random.default_rng(21).choice([-1, 1], size=32).astype(np.int8)
     R = OracleREWL("ea", 4, 2, 0.75, 2, 0.8, 1e-6, 4, couplings=J)
     E_ex, g_ex = X.enumerate_dos(4, "ea", couplings=J)
-    assert R.e_min == min(E_ex) and R.e_max == max(E_ex)   # the descent found the ground energy
+    # the grid reaches from the descent's lowest energy on down to -2N (nothing locked out)
+    assert R.e_min <= min(E_ex) and R.e_max == -R.e_min and R.e_min >= -2 * R.N and (min(E_ex) - R.e_min) % 4 == 0
     _run(R)
     assert _max_abs_error(R, E_ex, g_ex) < 0.08
 
