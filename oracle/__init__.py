@@ -70,6 +70,7 @@ def lib():
         L.orc_get_windows.argtypes = [P, P, P, P, P]
         L.orc_get_phase.argtypes = [P, P]
         L.orc_get_window_layout.argtypes = [P, P, P]
+        L.orc_get_replicas.argtypes = [P, P, P, P]
         L.orc_walker_all_seen.argtypes = [P, ctypes.c_int]
         L.orc_walker_all_seen.restype = ctypes.c_int
         L.orc_get_walkers.argtypes = [P, P, P, P, P]
@@ -193,6 +194,13 @@ class OracleREWL:
     def energy(self, spins):
         s = np.ascontiguousarray(spins, dtype=np.uint8)
         return int(self._lib.orc_energy(self._h, _ptr(s)))
+
+    def replicas(self):
+        """rep_id[W] (the replica walker W holds), rep_state and rep_trips per replica."""
+        n = self.h * self.m
+        rid, rst, rtr = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int64)
+        self._lib.orc_get_replicas(self._h, _ptr(rid), _ptr(rst), _ptr(rtr))
+        return {"rep_id": rid, "rep_state": rst, "rep_trips": rtr}
 
     def walker_all_seen(self, W):
         return bool(self._lib.orc_walker_all_seen(self._h, W))

@@ -351,6 +351,13 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
   R->near_ties = (uint64_t*)calloc((size_t)n_walkers, sizeof(uint64_t));
   R->x_tried = (uint64_t*)calloc((size_t)h, sizeof(uint64_t));
   R->x_accepted = (uint64_t*)calloc((size_t)h, sizeof(uint64_t));
+  R->rep_id = (int32_t*)calloc((size_t)n_walkers, sizeof(int32_t));
+  R->rep_state = (int32_t*)calloc((size_t)n_walkers, sizeof(int32_t));
+  R->rep_trips = (int64_t*)calloc((size_t)n_walkers, sizeof(int64_t));
+  for (int W = 0; W < n_walkers; ++W) {
+    R->rep_id[W] = W;
+    R->rep_state[W] = W < m ? 1 : 0; /* the replicas that start in the lowest window */
+  }
 
   for (int W = 0; W < n_walkers; ++W) {
     init_lattice(R, W);
@@ -409,6 +416,7 @@ void orc_destroy(orc_rewl* R) {
   free(R->Jr); free(R->Jd); free(R->Jb); free(R->spins); free(R->E); free(R->entry_t); free(R->seed_config);
   free(R->win_start); free(R->win_width); free(R->first_iter); free(R->lnf); free(R->iter); free(R->done); free(R->phase); free(R->lng); free(R->H);
   free(R->wl_accept); free(R->near_ties); free(R->x_tried); free(R->x_accepted);
+  free(R->rep_id); free(R->rep_state); free(R->rep_trips);
   free(R);
 }
 
@@ -503,6 +511,15 @@ static void exchange_pair(orc_rewl* R, int a, uint32_t round) {
       R->E[Wi] = EY;
       R->E[Wj] = EX;
       R->x_accepted[a]++;
+      /* the replicas travel with their configurations (Fig. 3: round trips) */
+      int32_t ri = R->rep_id[Wj], rj = R->rep_id[Wi];
+      R->rep_id[Wi] = ri;
+      R->rep_id[Wj] = rj;
+      if (a == 0) { /* replica ri arrives in the lowest window */
+        if (R->rep_state[ri] == 2) R->rep_trips[ri]++;
+        R->rep_state[ri] = 1;
+      }
+      if (a + 1 == R->h - 1 && R->rep_state[rj] == 1) R->rep_state[rj] = 2; /* rj reaches the highest */
     }
   }
   free(sigma);
@@ -666,6 +683,14 @@ void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* it
     if (lnf) lnf[a] = R->lnf[a];
     if (iter) iter[a] = R->iter[a];
     if (done) done[a] = R->done[a];
+  }
+}
+
+void orc_get_replicas(const orc_rewl* R, int32_t* rep_id, int32_t* rep_state, int64_t* rep_trips) {
+  for (int W = 0; W < R->h * R->m; ++W) {
+    if (rep_id) rep_id[W] = R->rep_id[W];
+    if (rep_state) rep_state[W] = R->rep_state[W];
+    if (rep_trips) rep_trips[W] = R->rep_trips[W];
   }
 }
 

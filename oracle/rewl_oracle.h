@@ -45,6 +45,12 @@ typedef struct orc_rewl {
   uint64_t sweep_clock;
   uint32_t xround;
   uint64_t *wl_accept, *near_ties, *x_tried, *x_accepted;
+  /* replica round trips (Fig. 3): rep_id[W] = the configuration (replica) walker W
+   * holds; per replica: rep_state 0 = not yet in the lowest window, 1 = has been
+   * there (heading up), 2 = has since reached the highest window (heading down);
+   * rep_trips = completed lowest -> highest -> lowest trips */
+  int32_t *rep_id, *rep_state;
+  int64_t* rep_trips;
 } orc_rewl;
 
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -59,6 +65,7 @@ void orc_info(const orc_rewl* R, int64_t* info);
 void orc_get_windows(const orc_rewl* R, int32_t* start, double* lnf, int32_t* iter, int32_t* done);
 void orc_get_phase(const orc_rewl* R, int32_t* phase);
 void orc_get_window_layout(const orc_rewl* R, int32_t* width, int64_t* first_iter);
+void orc_get_replicas(const orc_rewl* R, int32_t* rep_id, int32_t* rep_state, int64_t* rep_trips);
 int orc_walker_all_seen(const orc_rewl* R, int W);
 void orc_get_walkers(const orc_rewl* R, uint8_t* spins, int32_t* E, double* lng, uint32_t* H);
 void orc_get_couplings(const orc_rewl* R, int8_t* J);
