@@ -28,6 +28,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+def sites(wl):
+    """Sites of a workload's lattice: L^2, or L^3 on the cube."""
+    return wl["L"] ** 3 if wl["model"] == "ea3d" else wl["L"] ** 2
+
+
 WORKLOADS = {
     "ising-L32-h16-m4": dict(model="ising", L=32, q=2, h=16, m=4, lnf_final=1e-8,
                              desc="2D Ising L=32 periodic J=1; 16 windows at 75% overlap x 4 walkers (64 walkers); "
@@ -37,6 +42,9 @@ WORKLOADS = {
     "potts-q10-L32-h32-m16": dict(model="potts", L=32, q=10, h=32, m=16, lnf_final=1e-8,
                                   desc="2D q=10 Potts L=32; 32 windows at 75% overlap x 16 walkers (512 walkers); "
                                        "ln f 1 -> 1e-8"),
+    "ea3d-L12-h16-m4": dict(model="ea3d", L=12, q=2, h=16, m=4, lnf_final=1e-6,
+                            desc="3D +-J spin glass 12x12x12 periodic, couplings +-1 at p=1/2 from the seed; "
+                                 "16 windows at 75% overlap x 4 walkers; ln f 1 -> 1e-6"),
     "ising-L128-h128-m32": dict(model="ising", L=128, q=2, h=128, m=32, lnf_final=1e-6,
                                 desc="2D Ising L=128; 128 windows at 75% overlap x 32 walkers (4096 walkers); "
                                      "ln f 1 -> 1e-6"),
@@ -192,7 +200,7 @@ def oracle_rate(wl, seed, seconds):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    attempts = blocks * SPE * wl["L"] ** 2 * n_walk
+    attempts = blocks * SPE * O.N * n_walk
     return attempts / el, blocks, el
 
 
@@ -204,7 +212,7 @@ def run_reference(args, wl, world, rank):
 
     O = OracleREWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], 0, q=wl["q"],
                    sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
-    per_step = SPE * wl["L"] ** 2 * wl["h"] * wl["m"]
+    per_step = SPE * sites(wl) * wl["h"] * wl["m"]
     for _ in range(args.warmup):
         O.run_blocks(1)
     times = []
@@ -215,7 +223,7 @@ def run_reference(args, wl, world, rank):
     tot = sum(times)
     value = args.steps * per_step / tot
     sample = ("%d blocks of %d sweeps of the %s workload (%d walkers x %d sites) per step = 1/%d of a "
-              "flatness period" % (1, SPE, args.workload, wl["h"] * wl["m"], wl["L"] ** 2, SPF // SPE))
+              "flatness period" % (1, SPE, args.workload, wl["h"] * wl["m"], sites(wl), SPF // SPE))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -646,6 +654,48 @@ def run_time_to_dos(args, world, rank, local):
                                     "bit_identical_to_served": bits}}), flush=True)
 
 
+def run_glass_e0(args, world, rank, local):
+    """The 12^3 +-J glass: lowest energy per spin the REWL walk has visited
+    after a fixed time, over disorder realisations (seeds), beside the
+    paper's e_0 = -1.787 +- 0.005.  The zero-temperature descent that lays out
+    the windows is reported too: the walk can go below it (the lowest window
+    reaches on to -3N)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    wl = WORKLOADS["ea3d-L12-h16-m4"]
+    out = []
+    for sd in range(args.seed, args.seed + args.glass_samples):
+        D = rewl.REWL("ea3d", 12, wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd)
+        info = D.info
+        st0 = D.state()
+        e_desc = int(st0["E"].min())
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < args.glass_seconds:
+            if D.step(SPF):
+                break
+        el = time.perf_counter() - t0
+        st = D.state()
+        lng0 = st["lng"][:wl["m"]]                       # the lowest window's walkers
+        visited = np.nonzero((lng0 > 0).any(0))[0]
+        e_low = info["e_min"] + 4 * int(visited.min())
+        out.append({"seed": sd, "e_desc_per_spin": e_desc / 1728.0, "e_low_per_spin": e_low / 1728.0,
+                    "sweeps": int(st["sweep_clock"]), "seconds": el,
+                    "attempts_per_s": rewl.rewl_get_info(D._h)["attempts"] / el})
+        D.close()
+    lows = np.array([o["e_low_per_spin"] for o in out])
+    if rank == 0:
+        print(json.dumps({"metric": "lowest energy per spin visited by the REWL walk, 12^3 +-J glass, over seeds",
+                          "value": float(lows.mean()), "unit": "e_0 estimate (mean over samples)",
+                          "stderr": float(lows.std(ddof=1) / np.sqrt(len(lows))) if len(lows) > 1 else None,
+                          "paper_e0": "-1.787 +- 0.005", "n_gpus": world, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "glass-e0", "desc": wl["desc"], "seconds_per_sample": args.glass_seconds},
+                          "samples": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -653,7 +703,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["served-stream", "windows-balance", "rule-compare",
-                                                                        "time-to-dos"])
+                                                                        "time-to-dos", "glass-e0"])
     ap.add_argument("--mode", default="plain", choices=["plain", "graph"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=3)
@@ -672,6 +722,8 @@ def main():
     ap.add_argument("--rule-k", type=int, nargs="+", default=[16, 20], help="rule-compare: final ln f = 2^-k")
     ap.add_argument("--tdos-seeds", type=int, default=8, help="time-to-dos: seeds")
     ap.add_argument("--tdos-plain", type=int, default=1, help="time-to-dos: seeds also solved plain in full")
+    ap.add_argument("--glass-samples", type=int, default=4, help="glass-e0: disorder realisations")
+    ap.add_argument("--glass-seconds", type=float, default=60.0, help="glass-e0: walk time per realisation")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -681,6 +733,12 @@ def main():
             print(json.dumps({"impl": "reference", "unavailable": "the served stream has no CPU reference arm"}))
             return
         run_served(args, world, rank, local)
+        return
+    if args.workload == "glass-e0":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the glass e_0 run has no CPU reference arm"}))
+            return
+        run_glass_e0(args, world, rank, local)
         return
     if args.workload == "time-to-dos":
         if args.impl == "reference":

@@ -51,19 +51,22 @@ typedef enum {
   REWL_ENODEV = 9      /* no CUDA device, or the device is not sm_103 */
 } rewl_status;
 
-typedef enum { REWL_ISING = 0, REWL_POTTS = 1, REWL_EA_PM_J = 2 } rewl_model_kind;
+typedef enum { REWL_ISING = 0, REWL_POTTS = 1, REWL_EA_PM_J = 2, REWL_EA_PM_J_3D = 3 } rewl_model_kind;
 
 /* Model: kind; q = number of Potts states (2..16), ignored otherwise.
  * Ising: E = -sum_<ij> s_i s_j; +-J: E = -sum_<ij> J_ij s_i s_j with
  * J_ij = +-1; Potts: E = -sum_<ij> delta(s_i, s_j).  The sum runs over the
- * 2N nearest-neighbour bonds of the periodic square lattice. */
+ * 2N nearest-neighbour bonds of the periodic square lattice;
+ * REWL_EA_PM_J_3D is the +-J glass on the periodic L x L x L cube (the
+ * paper's 12^3 spin glass), 3N bonds, site i = (z L + y) L + x. */
 typedef struct {
   int32_t kind;
   int32_t q;
 } rewl_model;
 
-/* Lattice: dim must be 2, Lx == Ly == L with 2 <= L <= 256 (L even for +-J),
- * periodic must be 1. */
+/* Lattice: dim 2 with Lx == Ly == L, 2 <= L <= 256 (L even for +-J); or
+ * dim 3 (REWL_EA_PM_J_3D only) with Lx == Ly == L the edge of the cube,
+ * L even, 2 <= L <= 64; periodic must be 1. */
 typedef struct {
   int32_t dim, Lx, Ly, periodic;
 } rewl_lattice;
@@ -262,6 +265,12 @@ typedef struct {
                            the largest width, bins past a window's width stay 0) */
   int64_t* first_iter;  /* [windows] sweep clock at which the window's first merge happened, -1 before;
                            optional on set */
+  int32_t* rep_id;      /* [walkers] the replica (configuration, followed through the exchanges) that
+                           walker W holds; at creation walker W holds replica W */
+  int32_t* rep_state;   /* [replicas] 0 = not yet in the lowest window, 1 = has been there, 2 = has since
+                           reached the highest window */
+  int64_t* rep_trips;   /* [replicas] completed round trips lowest -> highest -> lowest window (Fig. 3);
+                           the three replica arrays are optional on set (all three or none) */
 } rewl_state;
 
 /* Copies the device state into the caller's buffers.  Errors: REWL_EINVAL,

@@ -81,7 +81,10 @@ rewl_ctx::~rewl_ctx() {
 // Energy windows: w = ceil(B / (1 + (h-1)(1-o))) bins, window k starting at
 // k(B-w)/(h-1) rounded half up (paper, Fig. 1a: equal-size windows, overlap o).
 // ---------------------------------------------------------------------------
-static rewl_status make_windows(int B, int h, double o, int* w_out, std::vector<int32_t>& start,
+// The equal partition covers the core bins [core_lo, core_lo + Bc) (all B bins
+// but for +-J, where the core is the descent's range); the first and the last
+// window then reach down to bin 0 and up to bin B-1.
+static rewl_status make_windows(int B, int h, double o, int core_lo, int Bc, int* w_out, std::vector<int32_t>& start,
                                 std::vector<int32_t>& width) {
   start.assign(h, 0);
   if (h == 1) {
@@ -89,14 +92,17 @@ static rewl_status make_windows(int B, int h, double o, int* w_out, std::vector<
     width.assign(1, B);
     return REWL_OK;
   }
-  int w = (int)std::ceil((double)B / (1.0 + (double)(h - 1) * (1.0 - o)));
-  if (w > B) w = B;
-  if (w < 3) return fail(REWL_EINVAL, "windows of %d bins are too narrow (B=%d, h=%d)", w, B, h);
-  for (int k = 0; k < h; ++k) start[k] = (int32_t)((2LL * k * (B - w) + (h - 1)) / (2LL * (h - 1)));
+  int w = (int)std::ceil((double)Bc / (1.0 + (double)(h - 1) * (1.0 - o)));
+  if (w > Bc) w = Bc;
+  if (w < 3) return fail(REWL_EINVAL, "windows of %d bins are too narrow (B=%d, h=%d)", w, Bc, h);
+  for (int k = 0; k < h; ++k) start[k] = core_lo + (int32_t)((2LL * k * (Bc - w) + (h - 1)) / (2LL * (h - 1)));
   for (int k = 0; k + 1 < h; ++k)
     if (start[k + 1] > start[k] + w - 1) return fail(REWL_EINVAL, "windows %d and %d do not overlap", k, k + 1);
-  *w_out = w;
   width.assign(h, w);
+  width[0] += start[0];
+  start[0] = 0;
+  width[h - 1] = B - start[h - 1];
+  *w_out = *std::max_element(width.begin(), width.end());
   return REWL_OK;
 }
 
@@ -249,14 +255,18 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   if (params) prm = *params;
   else rewl_params_default(&prm);
   const int kind = model->kind;
-  if (kind < 0 || kind > 2) return fail(REWL_EINVAL, "unknown model kind %d", kind);
+  if (kind < 0 || kind > 3) return fail(REWL_EINVAL, "unknown model kind %d", kind);
   if (kind == REWL_POTTS && (model->q < 2 || model->q > 16)) return fail(REWL_EINVAL, "Potts q=%d not in [2,16]", model->q);
-  if (lattice->dim != 2 || lattice->Lx != lattice->Ly || lattice->periodic != 1)
-    return fail(REWL_EINVAL, "only 2D periodic square lattices are supported");
+  const int dim = lattice->dim;
+  if ((dim != 2 && dim != 3) || lattice->Lx != lattice->Ly || lattice->periodic != 1 ||
+      (dim == 3) != (kind == REWL_EA_PM_J_3D))
+    return fail(REWL_EINVAL, "periodic square lattices, or the periodic cube for the 3D +-J model");
   const int L = lattice->Lx;
-  if (L < 2 || L > 256) return fail(REWL_EINVAL, "L=%d not in [2,256]", L);
-  if (kind == REWL_EA_PM_J && (L % 2)) return fail(REWL_EINVAL, "+-J needs an even L");
-  if (kind != REWL_EA_PM_J && couplings) return fail(REWL_EINVAL, "couplings are only taken by the +-J model");
+  if (L < 2 || L > (dim == 3 ? 64 : 256)) return fail(REWL_EINVAL, "L=%d not in [2,%d]", L, dim == 3 ? 64 : 256);
+  const bool pmj = kind == REWL_EA_PM_J || kind == REWL_EA_PM_J_3D;
+  if (pmj && (L % 2)) return fail(REWL_EINVAL, "+-J needs an even L");
+  if (!pmj && couplings) return fail(REWL_EINVAL, "couplings are only taken by the +-J models");
+  const int64_t N64 = dim == 3 ? (int64_t)L * L * L : (int64_t)L * L;
   if (windows < 1 || walkers_per_window < 1 || walkers_per_window > 4096 ||
       (int64_t)windows * walkers_per_window > (1 << 20))
     return fail(REWL_EINVAL, "windows=%d walkers_per_window=%d", windows, walkers_per_window);
@@ -268,7 +278,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   if (prm.sweeps_per_exchange < 1 || prm.sweeps_per_flat_check < prm.sweeps_per_exchange ||
       prm.sweeps_per_flat_check % prm.sweeps_per_exchange != 0)
     return fail(REWL_EINVAL, "sweeps_per_flat_check must be a positive multiple of sweeps_per_exchange");
-  if ((int64_t)prm.sweeps_per_exchange * L * L > 0x7fffffffLL) return fail(REWL_EINVAL, "sweeps_per_exchange too large");
+  if ((int64_t)prm.sweeps_per_exchange * N64 > 0x7fffffffLL) return fail(REWL_EINVAL, "sweeps_per_exchange too large");
   if (prm.entry_max_sweeps < 1 || prm.discovery_sweeps < 0) return fail(REWL_EINVAL, "entry/discovery sweeps");
   const int G = prm.lanes_per_walker;
   if (G != 0 && G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
@@ -286,8 +296,8 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
     return fail(REWL_EINVAL, "window_starts and window_widths go together");
   if (prm.prefetch_draws != 0 && prm.prefetch_draws != 1) return fail(REWL_EINVAL, "prefetch_draws %d", prm.prefetch_draws);
   if (couplings)
-    for (int i = 0; i < 2 * L * L; ++i)
-      if (couplings[i] != 1 && couplings[i] != -1) return fail(REWL_EINVAL, "coupling %d is %d", i, couplings[i]);
+    for (int64_t i = 0; i < dim * N64; ++i)
+      if (couplings[i] != 1 && couplings[i] != -1) return fail(REWL_EINVAL, "coupling %lld is %d", (long long)i, couplings[i]);
   rewl_status st = check_device();
   if (st != REWL_OK) return st;
 
@@ -298,10 +308,13 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   P.model = kind;
   P.q = kind == REWL_POTTS ? model->q : 2;
   P.L = L;
-  P.N = L * L;
+  P.N = (int)N64;
+  P.rows = dim == 3 ? L * L : L;
   P.Wr = kind == REWL_POTTS ? (L + 7) / 8 : (L + 31) / 32;
   P.Wr1 = (L + 31) / 32;
-  P.lat_words = L * P.Wr;
+  P.lat_words = P.rows * P.Wr;
+  P.j_words = dim * P.rows * P.Wr1;
+  P.magic_L2 = (uint32_t)(((1ull << 32) + (uint64_t)L * L - 1) / ((uint64_t)L * L));
   P.h = windows;
   P.m = walkers_per_window;
   P.n_walkers = windows * walkers_per_window;
@@ -325,25 +338,25 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   }
   if (cudaMallocHost(&c->h_n_done, 2 * sizeof(int32_t)) != cudaSuccess) return bail(fail(REWL_ENOMEM, "pinned alloc"));
 
-  // couplings: given, or drawn with p = 1/2 (bond b = 2i + d of site i, bit b
-  // of the coupling stream), packed as bit planes (bit 1 = J = -1)
-  const int nJ = 2 * L * P.Wr1;
+  // couplings: given, or drawn with p = 1/2 (bond b = dim i + d of site i,
+  // bit b of the coupling stream), packed as bit planes (bit 1 = J = -1)
+  const int nJ = P.j_words;
   std::vector<uint32_t> Jbits(nJ, 0u);
-  if (kind == REWL_EA_PM_J) {
+  if (pmj) {
     for (int i = 0; i < P.N; ++i) {
-      const int x = i % L, y = i / L;
-      for (int d = 0; d < 2; ++d) {
+      const int x = i % L, row = i / L;
+      for (int d = 0; d < dim; ++d) {
         bool neg;
         if (couplings) {
-          neg = couplings[2 * i + d] < 0;
+          neg = couplings[(int64_t)dim * i + d] < 0;
         } else {
-          const int b = 2 * i + d;
+          const int b = dim * i + d;
           const U4 r = philox10((uint32_t)(b / 128), 0u, 0xFFFFFFFFu, kTagCoupling, P.seed_lo, P.seed_hi);
           const int wi = (b % 128) / 32;
           const uint32_t wd = wi == 0 ? r.x : wi == 1 ? r.y : wi == 2 ? r.z : r.w;
           neg = (wd >> (b % 32)) & 1u;
         }
-        if (neg) Jbits[(d * L + y) * P.Wr1 + (x >> 5)] |= 1u << (x & 31);
+        if (neg) Jbits[(d * P.rows + row) * P.Wr1 + (x >> 5)] |= 1u << (x & 31);
       }
     }
   }
@@ -357,6 +370,9 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   S.win_start = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.win_width = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.first_iter = (int64_t*)c->dalloc(sizeof(int64_t) * P.h, &st);
+  S.rep_id = (int32_t*)c->dalloc(sizeof(int32_t) * P.n_walkers, &st);
+  S.rep_state = (int32_t*)c->dalloc(sizeof(int32_t) * P.n_walkers, &st);
+  S.rep_trips = (int64_t*)c->dalloc(sizeof(int64_t) * P.n_walkers, &st);
   S.lnf = (double*)c->dalloc(sizeof(double) * P.h, &st);
   S.iter = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
   S.done = (int32_t*)c->dalloc(sizeof(int32_t) * P.h, &st);
@@ -380,6 +396,16 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
     if (e_ != cudaSuccess) return bail(fail(REWL_ECUDA, "%s: %s", #expr, cudaGetErrorString(e_)));        \
   } while (0)
   BAIL_CUDA(h2d(c, S.J, Jbits.data(), sizeof(uint32_t) * nJ));
+  {  // every walker starts with its own replica; those of the lowest window have been there
+    std::vector<int32_t> id(nW), stt(nW);
+    for (int W = 0; W < nW; ++W) {
+      id[W] = W;
+      stt[W] = W < P.m ? 1 : 0;
+    }
+    BAIL_CUDA(h2d(c, S.rep_id, id.data(), sizeof(int32_t) * nW));
+    BAIL_CUDA(h2d(c, S.rep_state, stt.data(), sizeof(int32_t) * nW));
+    BAIL_CUDA(cudaMemsetAsync(S.rep_trips, 0, sizeof(int64_t) * nW, s));
+  }
   S.error = S.n_done + 1;
   BAIL_CUDA(cudaMemsetAsync(S.n_done, 0, 2 * sizeof(int32_t), s));
   BAIL_CUDA(cudaMemsetAsync(S.iter, 0, sizeof(int32_t) * P.h, s));
@@ -395,6 +421,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   BAIL_CUDA(launch_init(P, S, s));
 
   // energy range
+  int core_lo = 0, core_bins = 0;
   if (kind == REWL_ISING) {
     P.e_min = -2 * P.N;
     c->e_max = 2 * P.N;
@@ -413,12 +440,17 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
     for (int W = 1; W < nW; ++W)
       if (E[W] < best) best = E[W], bw = W;
     if (best >= 0) return bail(fail(REWL_EENTRY, "descent found no negative energy"));
-    P.e_min = best;
-    c->e_max = -best;
+    // windows over the descent's range [best, -best]; the grid, and the lowest and highest
+    // window, reach on to >= -dim N in steps of 4 so that lower energies can still be found
+    core_lo = (best + dim * P.N) / 4;
+    core_bins = (-2 * best) / 4 + 1;
+    P.e_min = best - 4 * core_lo;
+    c->e_max = -P.e_min;
     BAIL_CUDA(cudaMemcpyAsync(S.seed_config, S.lat + (size_t)bw * P.lat_words, sizeof(uint32_t) * P.lat_words,
                               cudaMemcpyDeviceToDevice, s));
   }
   P.n_bins = (c->e_max - P.e_min) / P.e_step + 1;
+  if (core_bins == 0) core_bins = P.n_bins;
   if (prm.window_starts) {
     st = check_windows(P.n_bins, P.h, prm.window_starts, prm.window_widths);
     if (st != REWL_OK) return bail(st);
@@ -426,7 +458,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
     c->win_width.assign(prm.window_widths, prm.window_widths + P.h);
     P.w = *std::max_element(c->win_width.begin(), c->win_width.end());
   } else {
-    st = make_windows(P.n_bins, P.h, overlap, &P.w, c->win_start, c->win_width);
+    st = make_windows(P.n_bins, P.h, overlap, core_lo, core_bins, &P.w, c->win_start, c->win_width);
     if (st != REWL_OK) return bail(st);
   }
   S.lng = (double*)c->dalloc(sizeof(double) * (size_t)nW * P.w, &st);
@@ -670,6 +702,9 @@ rewl_status rewl_get_state(rewl_handle c, rewl_state* st) {
   if (st->win_start) std::memcpy(st->win_start, c->win_start.data(), 4 * P.h);
   if (st->win_width) std::memcpy(st->win_width, c->win_width.data(), 4 * P.h);
   if (st->first_iter) CUDA_TRY(d2h(c, st->first_iter, c->S.first_iter, 8 * P.h));
+  if (st->rep_id) CUDA_TRY(d2h(c, st->rep_id, c->S.rep_id, 4 * nW));
+  if (st->rep_state) CUDA_TRY(d2h(c, st->rep_state, c->S.rep_state, 4 * nW));
+  if (st->rep_trips) CUDA_TRY(d2h(c, st->rep_trips, c->S.rep_trips, 8 * nW));
   if (st->lnf) CUDA_TRY(d2h(c, st->lnf, c->S.lnf, 8 * P.h));
   if (st->iteration) CUDA_TRY(d2h(c, st->iteration, c->S.iter, 4 * P.h));
   if (st->done) CUDA_TRY(d2h(c, st->done, c->S.done, 4 * P.h));
@@ -710,6 +745,17 @@ rewl_status rewl_set_state(rewl_handle c, const rewl_state* st) {
   CUDA_TRY(h2d(c, c->S.iter, st->iteration, 4 * P.h));
   CUDA_TRY(h2d(c, c->S.done, st->done, 4 * P.h));
   if (st->first_iter) CUDA_TRY(h2d(c, c->S.first_iter, st->first_iter, 8 * P.h));
+  if (st->rep_id && st->rep_state && st->rep_trips) {
+    std::vector<int> seen(nW, 0);
+    for (size_t W = 0; W < nW; ++W) {
+      if (st->rep_id[W] < 0 || st->rep_id[W] >= (int32_t)nW || seen[st->rep_id[W]]++)
+        return fail(REWL_EINVAL, "rep_id is not a permutation of the walkers");
+      if (st->rep_state[W] < 0 || st->rep_state[W] > 2) return fail(REWL_EINVAL, "rep_state[%zu]", W);
+    }
+    CUDA_TRY(h2d(c, c->S.rep_id, st->rep_id, 4 * nW));
+    CUDA_TRY(h2d(c, c->S.rep_state, st->rep_state, 4 * nW));
+    CUDA_TRY(h2d(c, c->S.rep_trips, st->rep_trips, 8 * nW));
+  }
   if (st->stage) {
     for (int a = 0; a < P.h; ++a)
       if (st->stage[a] != 0 && (st->stage[a] != 1 || P.wl_rule != REWL_RULE_ONE_OVER_T))

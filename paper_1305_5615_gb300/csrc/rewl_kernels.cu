@@ -41,41 +41,69 @@ __device__ __forceinline__ int bond_e(const Problem& P, uint32_t a, uint32_t b, 
   if (P.model == kPotts) return a == b ? -1 : 0;
   return ((a ^ b ^ jneg) & 1u) ? 1 : -1;
 }
-__device__ __forceinline__ uint32_t g_jbit(const Problem& P, const uint32_t* J, int plane, int x, int y) {
-  if (P.model != kEA) return 0u;
-  return coupling_bit(J, P.Wr1, plane, P.L, x, y);
+// coupling bit of plane (0 right, 1 down, 2 behind) at (x, row); row = y in 2D, z L + y in 3D
+__device__ __forceinline__ uint32_t g_jbit(const Problem& P, const uint32_t* J, int plane, int x, int row) {
+  if (P.model != kEA && P.model != kEA3) return 0u;
+  return coupling_bit(J, P.Wr1, plane, P.rows, x, row);
 }
 __device__ int g_energy(const Problem& P, const uint32_t* lat, const uint32_t* J) {
   int E = 0;
-  for (int y = 0; y < P.L; ++y)
-    for (int x = 0; x < P.L; ++x) {
-      const uint32_t s = g_site(P, lat, x, y);
-      const int xr = x + 1 == P.L ? 0 : x + 1, yd = y + 1 == P.L ? 0 : y + 1;
-      E += bond_e(P, s, g_site(P, lat, xr, y), g_jbit(P, J, 0, x, y));
-      E += bond_e(P, s, g_site(P, lat, x, yd), g_jbit(P, J, 1, x, y));
-    }
+  const int L = P.L, nz = P.model == kEA3 ? L : 1;
+  for (int z = 0; z < nz; ++z)
+    for (int y = 0; y < L; ++y)
+      for (int x = 0; x < L; ++x) {
+        const int row = z * L + y;
+        const uint32_t s = g_site(P, lat, x, row);
+        const int xr = x + 1 == L ? 0 : x + 1, yd = y + 1 == L ? 0 : y + 1;
+        E += bond_e(P, s, g_site(P, lat, xr, row), g_jbit(P, J, 0, x, row));
+        E += bond_e(P, s, g_site(P, lat, x, z * L + yd), g_jbit(P, J, 1, x, row));
+        if (P.model == kEA3) {
+          const int zb = z + 1 == L ? 0 : z + 1;
+          E += bond_e(P, s, g_site(P, lat, x, zb * L + y), g_jbit(P, J, 2, x, row));
+        }
+      }
   return E;
 }
-__device__ int g_delta_e(const Problem& P, const uint32_t* lat, const uint32_t* J, int x, int y, uint32_t v) {
+// energy change when site (x, y, z) takes value v (z = 0 in 2D)
+__device__ int g_delta_e(const Problem& P, const uint32_t* lat, const uint32_t* J, int x, int y, int z, uint32_t v) {
   const int L = P.L;
   const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
   const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
-  const uint32_t s = g_site(P, lat, x, y);
-  const uint32_t nr = g_site(P, lat, xr, y), nl = g_site(P, lat, xl, y);
-  const uint32_t nd = g_site(P, lat, x, yd), nu = g_site(P, lat, x, yu);
-  const uint32_t jr = g_jbit(P, J, 0, x, y), jl = g_jbit(P, J, 0, xl, y);
-  const uint32_t jd = g_jbit(P, J, 1, x, y), ju = g_jbit(P, J, 1, x, yu);
-  const int before = bond_e(P, s, nr, jr) + bond_e(P, s, nl, jl) + bond_e(P, s, nd, jd) + bond_e(P, s, nu, ju);
-  const int after = bond_e(P, v, nr, jr) + bond_e(P, v, nl, jl) + bond_e(P, v, nd, jd) + bond_e(P, v, nu, ju);
+  const int zo = z * L, row = zo + y;
+  const uint32_t s = g_site(P, lat, x, row);
+  const uint32_t nr = g_site(P, lat, xr, row), nl = g_site(P, lat, xl, row);
+  const uint32_t nd = g_site(P, lat, x, zo + yd), nu = g_site(P, lat, x, zo + yu);
+  const uint32_t jr = g_jbit(P, J, 0, x, row), jl = g_jbit(P, J, 0, xl, row);
+  const uint32_t jd = g_jbit(P, J, 1, x, row), ju = g_jbit(P, J, 1, x, zo + yu);
+  int before = bond_e(P, s, nr, jr) + bond_e(P, s, nl, jl) + bond_e(P, s, nd, jd) + bond_e(P, s, nu, ju);
+  int after = bond_e(P, v, nr, jr) + bond_e(P, v, nl, jl) + bond_e(P, v, nd, jd) + bond_e(P, v, nu, ju);
+  if (P.model == kEA3) {
+    const int zf = z ? z - 1 : L - 1, zb = z + 1 == L ? 0 : z + 1;
+    const uint32_t nb = g_site(P, lat, x, zb * L + y), nf = g_site(P, lat, x, zf * L + y);
+    const uint32_t jb = g_jbit(P, J, 2, x, row), jf = g_jbit(P, J, 2, x, zf * L + y);
+    before += bond_e(P, s, nb, jb) + bond_e(P, s, nf, jf);
+    after += bond_e(P, v, nb, jb) + bond_e(P, v, nf, jf);
+  }
   return after - before;
 }
 
-__device__ __forceinline__ void propose(const Problem& P, const uint32_t* lat, const U4& r, int& x, int& y,
-                                        uint32_t& v) {
-  const uint32_t site = scale32(r.x, (uint32_t)P.N);
+// The site of a draw: (x, y) on the square lattice, (x, y, z) on the cube.
+__device__ __forceinline__ void decode_site(const Problem& P, uint32_t site, int& x, int& y, int& z) {
+  if (P.model == kEA3) {
+    z = (int)mulhi32(site, P.magic_L2);
+    site -= (uint32_t)z * (uint32_t)(P.L * P.L);
+  } else {
+    z = 0;
+  }
   y = (int)mulhi32(site, P.magic_L);
   x = (int)site - y * P.L;
-  const uint32_t s = g_site(P, lat, x, y);
+}
+
+__device__ __forceinline__ void propose(const Problem& P, const uint32_t* lat, const U4& r, int& x, int& y, int& z,
+                                        uint32_t& v) {
+  const uint32_t site = scale32(r.x, (uint32_t)P.N);
+  decode_site(P, site, x, y, z);
+  const uint32_t s = g_site(P, lat, x, z * P.L + y);
   if (P.model == kPotts) {
     v = s + 1u + scale32(r.y, (uint32_t)(P.q - 1));
     if (v >= (uint32_t)P.q) v -= (uint32_t)P.q;
@@ -125,15 +153,15 @@ __device__ __forceinline__ int window_width(const Problem& P, const DevState& S,
 __device__ void greedy_move(const Problem& P, DevState& S, uint32_t* lat, int W, int lo, int hi, bool descent) {
   const uint64_t t = S.entry_t[W]++;
   const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagEntry, P.seed_lo, P.seed_hi);
-  int x, y;
+  int x, y, z;
   uint32_t v;
-  propose(P, lat, r, x, y, v);
+  propose(P, lat, r, x, y, z, v);
   const int E = S.E[W];
-  const int En = E + g_delta_e(P, lat, S.J, x, y, v);
+  const int En = E + g_delta_e(P, lat, S.J, x, y, z, v);
   const int before = descent ? E : window_distance(E, lo, hi);
   const int after = descent ? En : window_distance(En, lo, hi);
   if (after <= before) {
-    g_set_site(P, lat, x, y, v);
+    g_set_site(P, lat, x, z * P.L + y, v);
     S.E[W] = En;
   }
 }
@@ -177,6 +205,53 @@ __global__ void k_entry(Problem P, DevState S, uint64_t budget) {
 // the per-visit additions ln g += ln f (add_pow2_repeated), so the hot loop
 // issues no FP64 instruction.
 // ---------------------------------------------------------------------------
+// Site and proposal of a trial from its draw: (x, y) and the Potts offset on
+// the square lattice; (x, y) and z (carried in pv) on the cube.
+template <int MODEL>
+__device__ __forceinline__ void trial_site(const Problem& P, const U4& r, int& x, int& y, uint32_t& pv) {
+  const uint32_t site = scale32(r.x, (uint32_t)P.N);
+  if constexpr (MODEL == kEA3) {
+    const uint32_t z = mulhi32(site, P.magic_L2);
+    const uint32_t rem = site - z * (uint32_t)(P.L * P.L);
+    y = (int)mulhi32(rem, P.magic_L);
+    x = (int)rem - y * P.L;
+    pv = z;
+  } else {
+    y = (int)mulhi32(site, P.magic_L);
+    x = (int)site - y * P.L;
+    pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+  }
+}
+
+// Bit k set iff trial k < lane of this group of G moves a site of this
+// trial's neighbourhood (the site and its 4, or on the cube 6, neighbours).
+template <int MODEL, int G>
+__device__ __forceinline__ uint32_t conflict_mask(const Problem& P, int x, int y, uint32_t pv, int lane,
+                                                  uint32_t gm) {
+  const int L = P.L;
+  const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
+  const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
+  const uint32_t zk = MODEL == kEA3 ? pv << 16 : 0u;
+  const uint32_t key = (uint32_t)x | ((uint32_t)y << 8) | zk;
+  const uint32_t kl = (uint32_t)xl | ((uint32_t)y << 8) | zk, kr = (uint32_t)xr | ((uint32_t)y << 8) | zk;
+  const uint32_t ku = (uint32_t)x | ((uint32_t)yu << 8) | zk, kd = (uint32_t)x | ((uint32_t)yd << 8) | zk;
+  uint32_t kf = key, kb = key;
+  if constexpr (MODEL == kEA3) {
+    const uint32_t z = pv, zf = z ? z - 1 : (uint32_t)L - 1, zb = z + 1 == (uint32_t)L ? 0u : z + 1;
+    kf = (uint32_t)x | ((uint32_t)y << 8) | (zf << 16);
+    kb = (uint32_t)x | ((uint32_t)y << 8) | (zb << 16);
+  }
+  uint32_t M = 0;
+#pragma unroll
+  for (int i = 0; i < G - 1; ++i) {
+    const uint32_t pi = __shfl_sync(gm, key, i, G);
+    bool hit = pi == key || pi == kl || pi == kr || pi == ku || pi == kd;
+    if constexpr (MODEL == kEA3) hit = hit || pi == kf || pi == kb;
+    M |= (hit && i < lane) ? (1u << i) : 0u;
+  }
+  return M;
+}
+
 template <int G>
 __device__ __forceinline__ uint32_t group_mask() {
   if (G == 32) return 0xffffffffu;
@@ -243,7 +318,24 @@ __device__ __forceinline__ TrialEval<MODEL> eval_trial(const Problem& P, const u
   const int xl = x ? x - 1 : L - 1, xr = x + 1 == L ? 0 : x + 1;
   const int yu = y ? y - 1 : L - 1, yd = y + 1 == L ? 0 : y + 1;
   TrialEval<MODEL> t;
-  if constexpr (MODEL == kPotts) {
+  if constexpr (MODEL == kEA3) {  // the cube: pv carries z, rows are z * L + y
+    const int z = (int)pv, zo = z * L, row = zo + y;
+    const int zf = z ? z - 1 : L - 1, zb = z + 1 == L ? 0 : z + 1;
+    const uint32_t c = spin_bit(s_lat, wpb, lw, Wr, x, row);
+    const uint32_t nr = spin_bit(s_lat, wpb, lw, Wr, xr, row), nl = spin_bit(s_lat, wpb, lw, Wr, xl, row);
+    const uint32_t nd = spin_bit(s_lat, wpb, lw, Wr, x, zo + yd), nu = spin_bit(s_lat, wpb, lw, Wr, x, zo + yu);
+    const uint32_t nb = spin_bit(s_lat, wpb, lw, Wr, x, zb * L + y), nf = spin_bit(s_lat, wpb, lw, Wr, x, zf * L + y);
+    const int R = P.rows;
+    const uint32_t jr = coupling_bit(s_J, P.Wr1, 0, R, x, row), jl = coupling_bit(s_J, P.Wr1, 0, R, xl, row);
+    const uint32_t jd = coupling_bit(s_J, P.Wr1, 1, R, x, row), ju = coupling_bit(s_J, P.Wr1, 1, R, x, zo + yu);
+    const uint32_t jb = coupling_bit(s_J, P.Wr1, 2, R, x, row), jf = coupling_bit(s_J, P.Wr1, 2, R, x, zf * L + y);
+    const int sat = (int)(((c ^ nr ^ jr) & 1u) == 0) + (int)(((c ^ nl ^ jl) & 1u) == 0) +
+                    (int)(((c ^ nd ^ jd) & 1u) == 0) + (int)(((c ^ nu ^ ju) & 1u) == 0) +
+                    (int)(((c ^ nb ^ jb) & 1u) == 0) + (int)(((c ^ nf ^ jf) & 1u) == 0);
+    t.dbin = sat - 3;  // dE = 4 * satisfied - 12
+    t.widx = (uint32_t)((row * Wr + (x >> 5)) * wpb + lw);
+    t.wmask = 1u << (x & 31);
+  } else if constexpr (MODEL == kPotts) {
     const uint32_t v = potts_val(s_lat, wpb, lw, Wr, x, y);
     uint32_t nv = v + 1u + pv;
     if (nv >= (uint32_t)P.q) nv -= (uint32_t)P.q;
@@ -317,8 +409,8 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
     const int l = i / P.lat_words, j = i - l * P.lat_words;
     s_lat[j * wpb + l] = S.lat[(size_t)S.active[first + l] * P.lat_words + j];
   }
-  if (MODEL == kEA)
-    for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
+  if (MODEL == kEA || MODEL == kEA3)
+    for (int i = tid; i < P.j_words; i += nthr) s_J[i] = S.J[i];
   __syncthreads();
 
   const int lw = tid / G, lane = tid % G;
@@ -351,27 +443,15 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
       {
         const uint64_t t = t0 + base + (uint32_t)lane;
         const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-        const uint32_t site = scale32(r.x, (uint32_t)P.N);
-        const int y = (int)mulhi32(site, P.magic_L);
-        const int x = (int)site - y * L;
-        const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+        int x, y;
+        uint32_t pv;
+        trial_site<MODEL>(P, r, x, y, pv);
         const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
         tr.thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
         const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
         const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
         uint32_t M = 0;
-        if constexpr (G > 1) {
-          const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
-          const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
-          const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
-          const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
-#pragma unroll
-          for (int i = 0; i < G - 1; ++i) {
-            const uint32_t pi = __shfl_sync(gm, pk, i, G);
-            const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
-            M |= (hit && i < lane) ? (1u << i) : 0u;
-          }
-        }
+        if constexpr (G > 1) M = conflict_mask<MODEL, G>(P, x, y, pv, lane, gm);
         tr.pk = (uint32_t)(ev.dbin + 8) | (pv << 8) | (pk << 16);
         tr.mask = M;
         tr.widx = ev.widx;
@@ -567,26 +647,13 @@ __device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, l
 template <int MODEL>
 __device__ __forceinline__ PreTrial make_pretrial(const Problem& P, uint64_t t, int W, int lane) {
   const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-  const uint32_t site = scale32(r.x, (uint32_t)P.N);
-  const int y = (int)mulhi32(site, P.magic_L);
-  const int x = (int)site - y * P.L;
-  const uint32_t pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+  int x, y;
+  uint32_t pv;
+  trial_site<MODEL>(P, r, x, y, pv);
   const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
   const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
-  const int L = P.L;
-  const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
-  const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
-  const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
-  const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
-  const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
-  uint32_t M = 0;
-#pragma unroll
-  for (int k = 0; k < 31; ++k) {
-    const uint32_t pi = __shfl_sync(0xffffffffu, pk, k);
-    const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
-    M |= (hit && k < lane) ? (1u << k) : 0u;
-  }
-  return PreTrial{pk | (pv << 16), M, thr};
+  const uint32_t M = conflict_mask<MODEL, 32>(P, x, y, pv, lane, 0xffffffffu);
+  return PreTrial{(uint32_t)x | ((uint32_t)y << 8) | (pv << 16), M, thr};
 }
 
 // Runs the sweeps of the nloc walkers wids[0..nloc) of one CTA (wpb walkers per CTA).
@@ -620,8 +687,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     const int l = i / P.lat_words, j = i - l * P.lat_words;
     s_lat[j * wpb + l] = S.lat[(size_t)wids[l] * P.lat_words + j];
   }
-  if (MODEL == kEA)
-    for (int i = tid; i < 2 * P.L * P.Wr1; i += nthr) s_J[i] = S.J[i];
+  if (MODEL == kEA || MODEL == kEA3)
+    for (int i = tid; i < P.j_words; i += nthr) s_J[i] = S.J[i];
   if (RING && tid == 0)
     for (int k = 0; k < kRingSlots; ++k) {
       mbar_init(&s_full[k], 32);
@@ -706,25 +773,10 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
         } else {
           const uint64_t t = t0 + base + (uint32_t)lane;
           const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-          const uint32_t site = scale32(r.x, (uint32_t)P.N);
-          y = (int)mulhi32(site, P.magic_L);
-          x = (int)site - y * L;
-          pv = MODEL == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+          trial_site<MODEL>(P, r, x, y, pv);
           const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
           tr.thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
-          if constexpr (G > 1) {
-            const uint32_t pk0 = (uint32_t)x | ((uint32_t)y << 8);
-            const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
-            const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
-            const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
-            const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
-#pragma unroll
-            for (int i = 0; i < G - 1; ++i) {
-              const uint32_t pi = __shfl_sync(gm, pk0, i, G);
-              const bool hit = pi == pk0 || pi == pl || pi == pr || pi == pu || pi == pd;
-              M |= (hit && i < lane) ? (1u << i) : 0u;
-            }
-          }
+          if constexpr (G > 1) M = conflict_mask<MODEL, G>(P, x, y, pv, lane, gm);
         }
         const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
         const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
@@ -889,7 +941,7 @@ __global__ void __launch_bounds__(64, 1) k_sweep_ring(Problem P, DevState S, Swe
 // few SMs when they free up.  Trials are padded to a multiple of 32, so every
 // warp is wholly in range or wholly out of it.
 // ---------------------------------------------------------------------------
-template <int G>
+template <int MODEL, int G>
 __global__ void __launch_bounds__(256) k_precompute(Problem P, uint64_t t0, uint32_t n_att, uint32_t stride,
                                                     PreTrial* __restrict__ out) {
   const uint64_t total = (uint64_t)P.n_walkers * stride;
@@ -899,42 +951,39 @@ __global__ void __launch_bounds__(256) k_precompute(Problem P, uint64_t t0, uint
     const uint32_t i = (uint32_t)(g - (uint64_t)W * stride);
     const uint64_t t = t0 + i;
     const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-    const uint32_t site = scale32(r.x, (uint32_t)P.N);
-    const int y = (int)mulhi32(site, P.magic_L);
-    const int x = (int)site - y * P.L;
-    const uint32_t pv = P.model == kPotts ? scale32(r.y, (uint32_t)(P.q - 1)) : 0u;
+    int x, y;
+    uint32_t pv;
+    trial_site<MODEL>(P, r, x, y, pv);
     const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
     const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
-    const int L = P.L;
-    const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
-    const uint32_t pl = (uint32_t)(x ? x - 1 : L - 1) | ((uint32_t)y << 8);
-    const uint32_t pr = (uint32_t)(x + 1 == L ? 0 : x + 1) | ((uint32_t)y << 8);
-    const uint32_t pu = (uint32_t)x | ((uint32_t)(y ? y - 1 : L - 1) << 8);
-    const uint32_t pd = (uint32_t)x | ((uint32_t)(y + 1 == L ? 0 : y + 1) << 8);
-    const int lane = (int)(i % G);
-    const uint32_t gm = group_mask<G>();
-    uint32_t M = 0;
-#pragma unroll
-    for (int k = 0; k < G - 1; ++k) {
-      const uint32_t pi = __shfl_sync(gm, pk, k, G);
-      const bool hit = pi == pk || pi == pl || pi == pr || pi == pu || pi == pd;
-      M |= (hit && k < lane) ? (1u << k) : 0u;
-    }
-    if (i < n_att) out[g] = PreTrial{pk | (pv << 16), M, thr};
+    const uint32_t M = conflict_mask<MODEL, G>(P, x, y, pv, (int)(i % G), group_mask<G>());
+    if (i < n_att) out[g] = PreTrial{(uint32_t)x | ((uint32_t)y << 8) | (pv << 16), M, thr};
   }
+}
+
+template <int MODEL>
+static cudaError_t launch_precompute_m(int G, const Problem& P, uint64_t t0, uint32_t n_att, uint32_t stride,
+                                       PreTrial* out, unsigned blocks, cudaStream_t st) {
+  switch (G) {
+    case 8: k_precompute<MODEL, 8><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
+    case 16: k_precompute<MODEL, 16><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
+    case 32: k_precompute<MODEL, 32><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_precompute(int G, const Problem& P, uint64_t t0, uint32_t n_att, uint32_t stride, PreTrial* out,
                               int max_blocks, cudaStream_t st) {
   const uint64_t threads = (uint64_t)P.n_walkers * stride;
   const unsigned blocks = (unsigned)std::min<uint64_t>((threads + 255) / 256, (uint64_t)std::max(1, max_blocks));
-  switch (G) {
-    case 8: k_precompute<8><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
-    case 16: k_precompute<16><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
-    case 32: k_precompute<32><<<blocks, 256, 0, st>>>(P, t0, n_att, stride, out); break;
-    default: return cudaErrorInvalidValue;
+  switch (P.model) {
+    case kIsing: return launch_precompute_m<kIsing>(G, P, t0, n_att, stride, out, blocks, st);
+    case kPotts: return launch_precompute_m<kPotts>(G, P, t0, n_att, stride, out, blocks, st);
+    case kEA: return launch_precompute_m<kEA>(G, P, t0, n_att, stride, out, blocks, st);
+    case kEA3: return launch_precompute_m<kEA3>(G, P, t0, n_att, stride, out, blocks, st);
   }
-  return cudaGetLastError();
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------------------
@@ -993,6 +1042,16 @@ __device__ __forceinline__ void exchange_body(const Problem& P, const DevState& 
       S.E[Wi] = EY;
       S.E[Wj] = EX;
       ++n_acc;
+      if (S.rep_id) {  // the replicas travel with their configurations
+        const int32_t ri = S.rep_id[Wj], rj = S.rep_id[Wi];
+        S.rep_id[Wi] = ri;
+        S.rep_id[Wj] = rj;
+        if (a == 0) {  // ri arrives in the lowest window
+          if (S.rep_state[ri] == 2) S.rep_trips[ri] += 1;
+          S.rep_state[ri] = 1;
+        }
+        if (a + 1 == P.h - 1 && S.rep_state[rj] == 1) S.rep_state[rj] = 2;  // rj reaches the highest
+      }
     }
   }
   if (n_acc) atomicAdd(reinterpret_cast<unsigned long long*>(&S.x_accepted[a]), (unsigned long long)n_acc);
@@ -1117,7 +1176,8 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch(const BatchSlot* __restr
   switch (P.model) {
     case kIsing: sweep_chain_body<kIsing, 32>(P, S, n_att, 1, &wid, 1); break;
     case kPotts: sweep_chain_body<kPotts, 32>(P, S, n_att, 1, &wid, 1); break;
-    default: sweep_chain_body<kEA, 32>(P, S, n_att, 1, &wid, 1); break;
+    case kEA: sweep_chain_body<kEA, 32>(P, S, n_att, 1, &wid, 1); break;
+    default: sweep_chain_body<kEA3, 32>(P, S, n_att, 1, &wid, 1); break;
   }
 }
 
@@ -1228,6 +1288,7 @@ cudaError_t prepare_sweep(int G, int model) {
     case kIsing: return prepare_sweep_m<kIsing>(G);
     case kPotts: return prepare_sweep_m<kPotts>(G);
     case kEA: return prepare_sweep_m<kEA>(G);
+    case kEA3: return prepare_sweep_m<kEA3>(G);
   }
   return cudaErrorInvalidValue;
 }
@@ -1263,7 +1324,7 @@ size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
   size_t b = variant == kSweepStaged ? (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4)
                                      : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
   if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);
-  if (P.model == kEA) b += (size_t)2 * P.L * P.Wr1 * 4;
+  if (P.model == kEA || P.model == kEA3) b += (size_t)P.j_words * 4;
   if (variant == kSweepRing) b += kRingBytes;
   return b;
 }
@@ -1275,6 +1336,7 @@ cudaError_t launch_sweep(int G, const Problem& P, const DevState& S, const Sweep
     case kIsing: return launch_sweep_m<kIsing>(G, P, S, A, smem, st);
     case kPotts: return launch_sweep_m<kPotts>(G, P, S, A, smem, st);
     case kEA: return launch_sweep_m<kEA>(G, P, S, A, smem, st);
+    case kEA3: return launch_sweep_m<kEA3>(G, P, S, A, smem, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -5,7 +5,7 @@
 //   E     i32 [n_walkers]              current energies
 //   lng   f64 [n_walkers][w]           ln g over the window's w bins
 //   H     u32 [n_walkers][w]           visit histogram of the iteration
-//   J     u32 [2][L][Wr1]              +-J couplings, bit 1 = J -1 (planes: right, down)
+//   J     u32 [dim][rows][Wr1]         +-J couplings, bit 1 = J -1 (planes: right, down[, behind])
 //   win_start i32 [h], win_width i32 [h] (P.w = the largest, the row stride of lng and H),
 //   lnf f64 [h], iter i32 [h], done i32 [h], stage i32 [h], first_iter i64 [h]
 //   counters u64: wl_accept / near_ties / exact_tests [n_walkers], x_tried / x_accepted [h]
@@ -14,18 +14,21 @@
 
 namespace rewl {
 
-enum Model : int { kIsing = 0, kPotts = 1, kEA = 2 };
+enum Model : int { kIsing = 0, kPotts = 1, kEA = 2, kEA3 = 3 };  // kEA3: +-J on the L x L x L cube
 // 4th Philox counter word: one stream per purpose.
 enum Tag : uint32_t { kTagFlip = 0, kTagEntry = 1, kTagPerm = 2, kTagXacc = 3, kTagInit = 4, kTagCoupling = 5 };
 
 struct Problem {
   int model, q, L, N;
+  int rows;        // lattice rows: L (2D), L * L (3D: row = z * L + y)
   int Wr;          // words per lattice row (1-bit or 4-bit sites)
   int Wr1;         // words per row of a coupling plane
-  int lat_words;   // L * Wr
+  int lat_words;   // rows * Wr
+  int j_words;     // coupling words: dim planes (right, down[, behind]) of rows * Wr1
   int e_min, e_step, n_bins;
   int h, m, w, n_walkers;
-  uint32_t magic_L;  // ceil(2^32 / L): y = mulhi(site, magic_L) for site < N
+  uint32_t magic_L;   // ceil(2^32 / L): y = mulhi(site, magic_L) for site < L^2 (2D)
+  uint32_t magic_L2;  // ceil(2^32 / L^2): z = mulhi(site, magic_L2) for site < L^3 (3D)
   uint32_t seed_lo, seed_hi;
   int wl_rule;     // 0: flatness rule; 1: 1/t rule
   double flatness, lnf_final;
@@ -56,6 +59,12 @@ struct DevState {
   int32_t* win_width;    // [h] bins of each window (NULL: P.w for all)
   int64_t* first_iter;   // [h] sweep clock of each window's first merge, -1 before (may be NULL)
   int32_t* error;        // one word: bits set by a sweep kernel whose bounded wait ran out (may be NULL)
+  // replica round trips (Fig. 3): rep_id[W] = the replica (configuration) walker W holds;
+  // per replica: rep_state 0 = not yet in the lowest window, 1 = has been there, 2 = has since
+  // reached the highest window; rep_trips = completed lowest -> highest -> lowest trips
+  int32_t* rep_id;
+  int32_t* rep_state;
+  int64_t* rep_trips;
 };
 
 // Sweep kernel variants (identical results): the staged form keeps H in

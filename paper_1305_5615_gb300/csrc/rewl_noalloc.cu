@@ -113,7 +113,9 @@ extern "C" rewl_status rewl_sweep_noalloc(const rewl_sweep_desc* d, uint32_t* la
   P.N = L * L;
   P.Wr = d->model == REWL_POTTS ? (L + 7) / 8 : (L + 31) / 32;
   P.Wr1 = (L + 31) / 32;
+  P.rows = L;
   P.lat_words = L * P.Wr;
+  P.j_words = 2 * L * P.Wr1;
   P.e_min = d->e_min;
   P.e_step = d->e_step;
   P.h = d->windows;

@@ -79,17 +79,19 @@ struct Request {
 // Device bytes a request may use: its per-walker arrays with the widest
 // window its energy range allows, plus per-window tables.
 int64_t request_bytes(const Request& r) {
-  const int L = r.lattice.Lx, N = L * L;
+  const int L = r.lattice.Lx, dim = r.lattice.dim;
+  const int64_t rows = dim == 3 ? (int64_t)L * L : L, N = rows * L;
   const bool potts = r.model.kind == REWL_POTTS;
   const int Wr = potts ? (L + 7) / 8 : (L + 31) / 32, Wr1 = (L + 31) / 32;
-  const int64_t lat_words = (int64_t)L * Wr;
-  const int64_t B = potts ? 2LL * N + 1 : (int64_t)N + 1;
+  const int64_t lat_words = rows * Wr;
+  const int64_t B = potts ? 2LL * N + 1 : (int64_t)dim * N / 2 + 1;  // the widest grid the model can have
   int64_t w = B;
   if (r.windows > 1)
     w = std::min<int64_t>(B, (int64_t)std::ceil((double)B / (1.0 + (double)(r.windows - 1) * (1.0 - r.overlap))));
+  w = std::min<int64_t>(B, 2 * w);  // first and last windows reach on to the ends of a +-J grid
   const int64_t nW = (int64_t)r.windows * r.walkers_per_window;
-  return nW * (lat_words * 4 + 4 + w * 12 + 3 * 8 + 3 * 4 + 8) + (int64_t)r.windows * 48 + lat_words * 4 +
-         2LL * L * Wr1 * 4 + 4096;
+  return nW * (lat_words * 4 + 4 + w * 12 + 3 * 8 + 3 * 4 + 8) + (int64_t)r.windows * 64 + lat_words * 4 +
+         (int64_t)dim * rows * Wr1 * 4 + 4096;
 }
 
 // Running requests of one shape (model, L) and the device tables of their rounds.
@@ -442,18 +444,21 @@ rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, in
 rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* q, uint64_t* id) {
   if (!s || !q || !id) return sfail(REWL_EINVAL, "NULL argument");
   const int L = q->lattice.Lx;
-  if (q->model.kind < 0 || q->model.kind > 2 || q->lattice.dim != 2 || q->lattice.Lx != q->lattice.Ly ||
-      q->lattice.periodic != 1 || L < 2 || L > 256 || q->windows < 1 || q->walkers_per_window < 1 ||
-      q->walkers_per_window > 4096 || !(q->overlap > 0.0 && q->overlap < 1.0))
+  const int dim = q->lattice.dim;
+  if (q->model.kind < 0 || q->model.kind > 3 || (dim != 2 && dim != 3) ||
+      (dim == 3) != (q->model.kind == REWL_EA_PM_J_3D) || q->lattice.Lx != q->lattice.Ly ||
+      q->lattice.periodic != 1 || L < 2 || L > (dim == 3 ? 64 : 256) || q->windows < 1 ||
+      q->walkers_per_window < 1 || q->walkers_per_window > 4096 || !(q->overlap > 0.0 && q->overlap < 1.0))
     return sfail(REWL_EINVAL, "invalid request");
-  if (q->model.kind != REWL_EA_PM_J && q->couplings) return sfail(REWL_EINVAL, "couplings are only taken by +-J");
+  const bool pmj = q->model.kind == REWL_EA_PM_J || q->model.kind == REWL_EA_PM_J_3D;
+  if (!pmj && q->couplings) return sfail(REWL_EINVAL, "couplings are only taken by +-J");
   std::lock_guard<std::mutex> lock(s->mu);
   Request r;
   r.id = s->next_id++;
   r.model = q->model;
   r.lattice = q->lattice;
   if (q->couplings) {
-    r.couplings.assign(q->couplings, q->couplings + 2 * L * L);
+    r.couplings.assign(q->couplings, q->couplings + (dim == 3 ? 3LL * L * L * L : 2LL * L * L));
     r.has_couplings = true;
   }
   r.windows = q->windows;

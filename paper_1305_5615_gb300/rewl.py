@@ -14,9 +14,9 @@ import numpy as np
 
 from . import _build
 
-ISING, POTTS, EA_PM_J = 0, 1, 2
+ISING, POTTS, EA_PM_J, EA_PM_J_3D = 0, 1, 2, 3
 MODE_PLAIN, MODE_GRAPH = 0, 1
-MODELS = {"ising": ISING, "potts": POTTS, "ea": EA_PM_J, "pmj": EA_PM_J}
+MODELS = {"ising": ISING, "potts": POTTS, "ea": EA_PM_J, "pmj": EA_PM_J, "ea3d": EA_PM_J_3D}
 RULE_FLAT, RULE_ONE_OVER_T = 0, 1
 WL_RULES = {"flat": RULE_FLAT, "1/t": RULE_ONE_OVER_T}
 
@@ -98,7 +98,8 @@ class rewl_state(ctypes.Structure):
                 ("lattice", "E", "lng", "H", "win_start", "lnf", "iteration", "done", "wl_accept", "near_ties",
                  "exact_tests", "x_tried", "x_accepted")] + \
                [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("stage", ctypes.c_void_p),
-                ("win_width", ctypes.c_void_p), ("first_iter", ctypes.c_void_p)]
+                ("win_width", ctypes.c_void_p), ("first_iter", ctypes.c_void_p), ("rep_id", ctypes.c_void_p),
+                ("rep_state", ctypes.c_void_p), ("rep_trips", ctypes.c_void_p)]
 
 
 _lib = None
@@ -193,6 +194,9 @@ def rewl_create(model, lattice, couplings, windows, overlap, walkers_per_window,
                 params=None):
     h = ctypes.c_void_p()
     cpl = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
+    if cpl is not None and cpl.size != lattice.dim * lattice.Lx ** lattice.dim:
+        raise ValueError("couplings: %d values for %d sites in %d dimensions" %
+                         (cpl.size, lattice.Lx ** lattice.dim, lattice.dim))
     st = load().rewl_create(ctypes.byref(h), ctypes.byref(model), ctypes.byref(lattice), _p(cpl), windows, overlap,
                             walkers_per_window, flatness, lnf_final, ctypes.c_uint64(seed),
                             ctypes.byref(params) if params is not None else None)
@@ -237,7 +241,8 @@ def rewl_get_state(h, info):
          "done": np.zeros(hw, np.int32), "wl_accept": np.zeros(nW, np.uint64), "near_ties": np.zeros(nW, np.uint64),
          "exact_tests": np.zeros(nW, np.uint64), "x_tried": np.zeros(hw, np.uint64),
          "x_accepted": np.zeros(hw, np.uint64), "stage": np.zeros(hw, np.int32), "win_width": np.zeros(hw, np.int32),
-         "first_iter": np.zeros(hw, np.int64)}
+         "first_iter": np.zeros(hw, np.int64), "rep_id": np.zeros(nW, np.int32), "rep_state": np.zeros(nW, np.int32),
+         "rep_trips": np.zeros(nW, np.int64)}
     s = rewl_state(**{k: _p(v) for k, v in a.items()})
     _check(load().rewl_get_state(h, ctypes.byref(s)), "rewl_get_state")
     a["sweep_clock"], a["exchange_rounds"] = s.sweep_clock, s.exchange_rounds
@@ -350,7 +355,8 @@ class REWL:
             p.alloc, p.free = self._keep
         self.params = p
         self._h = None
-        self._h = rewl_create(rewl_model(model, q), rewl_lattice(2, L, L, 1), couplings, windows, overlap,
+        dim = 3 if model == EA_PM_J_3D else 2
+        self._h = rewl_create(rewl_model(model, q), rewl_lattice(dim, L, L, 1), couplings, windows, overlap,
                               walkers_per_window, flatness, lnf_final, seed, p)
         self.info = rewl_get_info(self._h)
 
@@ -420,7 +426,10 @@ class RewlServer:
         if isinstance(model, str):
             model = MODELS[model]
         cpl = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
-        r = rewl_request(rewl_model(model, q), rewl_lattice(2, L, L, 1), _p(cpl), windows, overlap,
+        if cpl is not None and cpl.size != (3 * L ** 3 if model == EA_PM_J_3D else 2 * L * L):
+            raise ValueError("couplings: wrong number of values")
+        r = rewl_request(rewl_model(model, q), rewl_lattice(3 if model == EA_PM_J_3D else 2, L, L, 1), _p(cpl),
+                         windows, overlap,
                          walkers_per_window, flatness, lnf_final, seed)
         rid = ctypes.c_uint64()
         _check(load().rewl_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "rewl_server_submit")
@@ -448,19 +457,21 @@ class RewlServer:
 
 
 def unpack_lattice(words, L, model):
-    """Packed configurations [walkers][lattice_words] -> site values [walkers][L*L]
-    (site i = y*L + x), following the layout documented in include/rewl.h."""
+    """Packed configurations [walkers][lattice_words] -> site values [walkers][N]
+    (site i = y*L + x; on the cube i = (z*L + y)*L + x, row z*L + y), following
+    the layout documented in include/rewl.h."""
     words = np.asarray(words, dtype=np.uint32)
     n = words.shape[0]
-    out = np.zeros((n, L * L), np.uint8)
+    rows = L * L if model == EA_PM_J_3D else L
+    out = np.zeros((n, rows * L), np.uint8)
     if model == POTTS:
         Wr = (L + 7) // 8
-        for y in range(L):
+        for y in range(rows):
             for x in range(L):
                 out[:, y * L + x] = (words[:, y * Wr + x // 8] >> (4 * (x % 8))) & 15
     else:
         Wr = (L + 31) // 32
-        for y in range(L):
+        for y in range(rows):
             for x in range(L):
                 out[:, y * L + x] = (words[:, y * Wr + x // 32] >> (x % 32)) & 1
     return out

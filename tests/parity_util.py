@@ -52,6 +52,9 @@ def compare_states(O, D, where=""):
     assert np.array_equal(sg["near_ties"], co["near_ties"]), where
     assert np.array_equal(sg["x_tried"], co["x_tried"]), where
     assert np.array_equal(sg["x_accepted"], co["x_accepted"]), where
+    rp = O.replicas()
+    for k in ("rep_id", "rep_state", "rep_trips"):
+        assert np.array_equal(sg[k], rp[k]), (where, k)
     assert sg["sweep_clock"] == O.info()["sweep_clock"], where
     return 0
 
