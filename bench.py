@@ -684,6 +684,7 @@ def run_glass_e0(args, world, rank, local):
         e_low = info["e_min"] + 4 * int(visited.min())
         out.append({"seed": sd, "e_desc_per_spin": e_desc / 1728.0, "e_low_per_spin": e_low / 1728.0,
                     "sweeps": int(st["sweep_clock"]), "seconds": el,
+                    "round_trips": int(st["rep_trips"].sum()), "replicas": int(len(st["rep_trips"])),
                     "attempts_per_s": rewl.rewl_get_info(D._h)["attempts"] / el})
         D.close()
     lows = np.array([o["e_low_per_spin"] for o in out])

@@ -1181,6 +1181,56 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch(const BatchSlot* __restr
   }
 }
 
+// The same with a producer warp per walker (the ring form): for rounds with few
+// walkers on the GPU, where each walker's chain has an SM sub-partition of its own.
+__global__ void __launch_bounds__(64, 8) k_sweep_batch_ring(const BatchSlot* __restrict__ slots,
+                                                            const BatchWalker* __restrict__ list) {
+  __shared__ int32_t wid;
+  const BatchWalker bw = list[blockIdx.x];
+  const Problem P = slots[bw.slot].P;
+  const DevState S = slots[bw.slot].S;
+  const uint32_t n_att = slots[bw.slot].n_att;
+  if (!slots[bw.slot].active || S.done[bw.W / P.m]) return;  // uniform over the CTA
+  if (threadIdx.x == 0) wid = bw.W;
+  __syncthreads();
+  switch (P.model) {
+    case kIsing: sweep_chain_body<kIsing, 32, true>(P, S, n_att, 1, &wid, 1); break;
+    case kPotts: sweep_chain_body<kPotts, 32, true>(P, S, n_att, 1, &wid, 1); break;
+    case kEA: sweep_chain_body<kEA, 32, true>(P, S, n_att, 1, &wid, 1); break;
+    default: sweep_chain_body<kEA3, 32, true>(P, S, n_att, 1, &wid, 1); break;
+  }
+}
+
+// For rounds with many walkers on the GPU (the chains share the SMs and the
+// issue slots are what runs out): up to 4 walkers of one request per CTA, 8
+// lanes each, so that one instruction of the sequential step serves 4 chains.
+// Entry (slot, W0) covers walkers W0 .. W0+3 of the slot; walkers of finished
+// windows are left out.
+__global__ void __launch_bounds__(32, 16) k_sweep_batch_quad(const BatchSlot* __restrict__ slots,
+                                                             const BatchWalker* __restrict__ list) {
+  __shared__ int32_t wids[4];
+  __shared__ int32_t nloc;
+  const BatchWalker bw = list[blockIdx.x];
+  const Problem P = slots[bw.slot].P;
+  const DevState S = slots[bw.slot].S;
+  const uint32_t n_att = slots[bw.slot].n_att;
+  if (!slots[bw.slot].active) return;  // uniform over the CTA
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int W = bw.W; W < bw.W + 4 && W < P.n_walkers; ++W)
+      if (!S.done[W / P.m]) wids[n++] = W;
+    nloc = n;
+  }
+  __syncthreads();
+  if (nloc == 0) return;  // uniform over the CTA
+  switch (P.model) {
+    case kIsing: sweep_chain_body<kIsing, 8>(P, S, n_att, 4, wids, nloc); break;
+    case kPotts: sweep_chain_body<kPotts, 8>(P, S, n_att, 4, wids, nloc); break;
+    case kEA: sweep_chain_body<kEA, 8>(P, S, n_att, 4, wids, nloc); break;
+    default: sweep_chain_body<kEA3, 8>(P, S, n_att, 4, wids, nloc); break;
+  }
+}
+
 __global__ void k_exchange_batch(const BatchSlot* __restrict__ slots, int max_pairs) {
   const int s = (int)blockIdx.x / max_pairs, p = (int)blockIdx.x % max_pairs;
   if (!slots[s].active) return;
@@ -1225,13 +1275,24 @@ __global__ void k_slot_report(const BatchSlot* __restrict__ slots, int n_slots, 
 // allowance stays below the 227 KB per-CTA limit.
 constexpr int kBatchDynSmem = 226 * 1024;
 
+size_t ring_extra_smem() { return kRingBytes; }
+size_t batch_smem_limit() { return kBatchDynSmem; }
+
 cudaError_t prepare_sweep_batch() {
-  return cudaFuncSetAttribute(k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  if (e != cudaSuccess) return e;
+  const cudaError_t e2 = cudaFuncSetAttribute(k_sweep_batch_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  if (e2 != cudaSuccess) return e2;
+  return cudaFuncSetAttribute(k_sweep_batch_ring, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
 }
 
 cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, const BatchWalker* d_list, int n_list,
-                               size_t smem, int max_pairs, int max_m, int max_h, cudaStream_t st) {
-  if (n_list > 0) k_sweep_batch<<<n_list, 32, smem, st>>>(d_slots, d_list);
+                               size_t smem, int max_pairs, int max_m, int max_h, int form, cudaStream_t st) {
+  if (n_list > 0) {
+    if (form == kBatchRing) k_sweep_batch_ring<<<n_list, 64, smem + kRingBytes, st>>>(d_slots, d_list);
+    else if (form == kBatchQuad) k_sweep_batch_quad<<<n_list, 32, smem, st>>>(d_slots, d_list);
+    else k_sweep_batch<<<n_list, 32, smem, st>>>(d_slots, d_list);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (max_pairs > 0) {

@@ -22,9 +22,14 @@ cudaError_t launch_descent(const Problem& P, const DevState& S, uint64_t n_att, 
 cudaError_t launch_entry(const Problem& P, const DevState& S, uint64_t budget, cudaStream_t st);
 
 // served form (rewl_server.cu)
+size_t ring_extra_smem();   // shared memory the ring form adds to a walker's CTA
+size_t batch_smem_limit();  // dynamic shared memory a batched sweep CTA may use
 cudaError_t prepare_sweep_batch();
 cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, const BatchWalker* d_list, int n_list,
-                               size_t smem, int max_pairs, int max_m, int max_h, cudaStream_t st);
+                               size_t smem, int max_pairs, int max_m, int max_h, int form, cudaStream_t st);
+// forms of the batched sweep: one walker per 32-lane CTA; the same with a producer warp
+// (list of walkers); up to 4 walkers of one request per CTA, 8 lanes each (list of quads)
+enum BatchForm : int { kBatchOne = 0, kBatchRing = 1, kBatchQuad = 2 };
 cudaError_t launch_slot_report(const BatchSlot* d_slots, int n_slots, SlotReport* out, cudaStream_t st);
 
 }  // namespace rewl

@@ -112,10 +112,10 @@ struct Group {
   BatchSlot* d_slots = nullptr;     // [cap]
   SlotReport* h_rep = nullptr;      // pinned [cap]
   SlotReport* d_rep = nullptr;      // [cap]
-  BatchWalker* h_list = nullptr;    // pinned [list_cap]
+  BatchWalker* h_list = nullptr;    // pinned [list_cap]: every walker, then (from n_list) every quad
   BatchWalker* d_list = nullptr;    // [list_cap]
-  int list_cap = 0, n_list = 0, hi = 0;  // hi: slots [0, hi) in the round
-  size_t smem = 0;
+  int list_cap = 0, n_list = 0, n_quad = 0, hi = 0;  // hi: slots [0, hi) in the round
+  size_t smem = 0, smem_quad = 0;
   int max_pairs = 0, max_m = 1, max_h = 1;
   bool dirty = true;
 
@@ -155,6 +155,15 @@ struct rewl_server {
   std::vector<std::unique_ptr<Group>> groups;
   int64_t rounds = 0, attempts = 0;
   int finished = 0, failed = 0;
+  int n_sm = 152;
+
+  int64_t running_walkers() const {
+    int64_t n = 0;
+    for (const auto& gp : groups)
+      for (size_t s = 0; s < gp->slots.size(); ++s)
+        if (gp->slot_req[s]) n += gp->slots[s].P.n_walkers;
+    return n;
+  }
 
   ~rewl_server() {
     for (auto& g : groups)
@@ -275,25 +284,28 @@ struct rewl_server {
       g.d_rep = dr;
       g.cap = cap;
     }
-    int n = 0, hi = 0;
+    int n = 0, nq = 0, hi = 0;
     g.max_pairs = 0;
     g.max_m = 1;
     g.max_h = 1;
     g.smem = 0;
+    g.smem_quad = 0;
     for (int s = 0; s < need; ++s) {
       g.h_stage[s] = g.slots[s];
       if (!g.slot_req[s]) continue;
       const Problem& P = g.slots[s].P;
       n += P.n_walkers;
+      nq += (P.n_walkers + 3) / 4;
       hi = s + 1;
       g.smem = std::max(g.smem, sweep_smem_bytes(P, 1, 32, kSweepChain));
+      g.smem_quad = std::max(g.smem_quad, sweep_smem_bytes(P, 4, 8, kSweepChain));
       g.max_pairs = std::max(g.max_pairs, P.h / 2);
       g.max_m = std::max(g.max_m, P.m);
       g.max_h = std::max(g.max_h, P.h);
     }
     g.hi = hi;
-    if (n > g.list_cap) {
-      const int cap = std::max(n, 2 * g.list_cap);
+    if (n + nq > g.list_cap) {
+      const int cap = std::max(n + nq, 2 * g.list_cap);
       BatchWalker *hl = nullptr, *dl = nullptr;
       if (cudaMallocHost(&hl, sizeof(BatchWalker) * cap) != cudaSuccess ||
           cudaMalloc(&dl, sizeof(BatchWalker) * cap) != cudaSuccess) {
@@ -312,9 +324,15 @@ struct rewl_server {
       if (!g.slot_req[s]) continue;
       for (int W = 0; W < g.slots[s].P.n_walkers; ++W) g.h_list[k++] = BatchWalker{s, W};
     }
+    for (int s = 0; s < hi; ++s) {
+      if (!g.slot_req[s]) continue;
+      for (int W = 0; W < g.slots[s].P.n_walkers; W += 4) g.h_list[k++] = BatchWalker{s, W};
+    }
     g.n_list = n;
+    g.n_quad = nq;
     if (hi) SCUDA(cudaMemcpyAsync(g.d_slots, g.h_stage, sizeof(BatchSlot) * hi, cudaMemcpyHostToDevice, g.stream));
-    if (n) SCUDA(cudaMemcpyAsync(g.d_list, g.h_list, sizeof(BatchWalker) * n, cudaMemcpyHostToDevice, g.stream));
+    if (n + nq)
+      SCUDA(cudaMemcpyAsync(g.d_list, g.h_list, sizeof(BatchWalker) * (n + nq), cudaMemcpyHostToDevice, g.stream));
     g.dirty = false;
     return REWL_OK;
   }
@@ -326,7 +344,20 @@ struct rewl_server {
       if (st != REWL_OK) return st;
     }
     if (g.n_list == 0) return REWL_OK;
-    SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list, g.n_list, g.smem, g.max_pairs, g.max_m, g.max_h, g.stream));
+    // few walkers on the GPU: each walker's chain has a sub-partition to itself, and a producer
+    // warp per walker makes its draws (the ring form); many walkers share the SMs and their issue
+    // slots, and 4 walkers per CTA with 8 lanes each share the instructions of the sequential step
+    const bool few = running_walkers() <= 8 * n_sm;
+    if (few && g.smem + ring_extra_smem() <= batch_smem_limit()) {
+      SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list, g.n_list, g.smem, g.max_pairs, g.max_m, g.max_h,
+                               kBatchRing, g.stream));
+    } else if (!few && g.smem_quad <= batch_smem_limit()) {
+      SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list + g.n_list, g.n_quad, g.smem_quad, g.max_pairs, g.max_m,
+                               g.max_h, kBatchQuad, g.stream));
+    } else {
+      SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list, g.n_list, g.smem, g.max_pairs, g.max_m, g.max_h,
+                               kBatchOne, g.stream));
+    }
     SCUDA(launch_slot_report(g.d_slots, g.hi, g.d_rep, g.stream));
     SCUDA(cudaMemcpyAsync(g.h_rep, g.d_rep, sizeof(SlotReport) * g.hi, cudaMemcpyDeviceToHost, g.stream));
     SCUDA(cudaEventRecord(g.ev, g.stream));
@@ -432,7 +463,10 @@ rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, in
   else rewl_params_default(&s->params);
   s->budget = device_bytes;
   s->max_running = max_running;
-  const cudaError_t e = prepare_sweep_batch();
+  cudaError_t e = prepare_sweep_batch();
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) {
     delete s;
     return sfail(REWL_ECUDA, "server set-up: %s", cudaGetErrorString(e));

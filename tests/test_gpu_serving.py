@@ -135,3 +135,30 @@ def test_one_shape_group_grows_and_shapes_run_side_by_side():
         assert info["sweeps"] == sweeps and info["attempts"] == attempts, seed
         assert np.array_equal(S.result(rid)[0].view(np.uint64), g.view(np.uint64)), seed
     assert st["attempts"] == sum(alone[s][2] for s in ids)
+
+
+def test_many_walkers_take_the_plain_chain_form_and_match_alone():
+    """Forty requests of 32 walkers (1280 > 8 per SM on 152 SMs) run the
+    batched sweep without producer warps; with the first three alone they run
+    it with them.  Either way the results equal the solves alone."""
+    reqs = [dict(model="ising", L=6, windows=4, walkers_per_window=8, lnf_final=1e-2, seed=300 + i, q=2)
+            for i in range(40)]
+    alone = {}
+    for r in reqs[:3] + reqs[-2:]:
+        D = rewl.REWL(r["model"], r["L"], r["windows"], 0.75, r["walkers_per_window"], 0.8, r["lnf_final"],
+                      r["seed"], q=r["q"])
+        assert D.step(0)
+        alone[r["seed"]] = D.lng()[0]
+        D.close()
+    for batch in (reqs[:3], reqs):
+        S = rewl.RewlServer(device_bytes=4 << 30, max_running=64)
+        ids = {r["seed"]: _submit(S, r) for r in batch}
+        for _ in range(100000):
+            st = S.run(20)
+            if st["running"] == 0 and st["queued"] == 0:
+                break
+        assert st["finished"] == len(batch)
+        for seed, g in alone.items():
+            if seed in ids:
+                assert np.array_equal(S.result(ids[seed])[0].view(np.uint64), g.view(np.uint64)), seed
+        S.close()
