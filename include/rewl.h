@@ -358,8 +358,9 @@ rewl_status rewl_thermo_jackknife(const double* lng_runs, int32_t n_runs, int32_
  * shape (model, L).  A group advances by rounds: for every request of the
  * group one block of sweeps_per_exchange sweeps, one exchange round and,
  * when due, the flatness check -- one fused launch for the sweeps of all the
- * group's walkers, one launch each for the exchanges, clocks and flatness
- * checks of all its requests.  Each group runs on a stream of its own, so
+ * group's walkers (with a producer warp per walker while the GPU holds few
+ * walkers, else 4 walkers of a request per CTA), one launch each for the
+ * exchanges, clocks and flatness checks of all its requests.  Each group runs on a stream of its own, so
  * groups of different sizes progress side by side at their own pace.
  * rewl_server_run issues a round for every idle group and returns once at
  * least one round has finished, per unit of max_rounds.  Finished requests
