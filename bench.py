@@ -245,9 +245,16 @@ def run_gb300(args, wl, world, rank, local):
     stream = torch.cuda.Stream()
     mode = rewl.MODE_GRAPH if args.mode == "graph" else rewl.MODE_PLAIN
 
+    tuned, tune_res = {}, None
+    if args.autotune:  # launch shape timed on this problem before the timed region (same bits either way)
+        tuned, tune_res = rewl.rewl_autotune(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS,
+                                             wl["lnf_final"], seed, q=wl["q"], sweeps=2 * SPE,
+                                             sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
+
     def make():
         return rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seed, q=wl["q"],
-                         sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF, stream=stream, profile=True, mode=mode)
+                         sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF, stream=stream, profile=True, mode=mode,
+                         **tuned)
 
     D = make()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -333,7 +340,11 @@ def run_gb300(args, wl, world, rank, local):
                            "lanes_per_walker": i1["lanes_per_walker"], "walkers_per_block": i1["walkers_per_block"],
                            "step": "one flatness period: 10 x (100 sweeps + exchange) + flatness/merge",
                            "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                           "parallelism": "replicas x%d (independent seeds)" % world},
+                           "parallelism": "replicas x%d (independent seeds)" % world,
+                           "launch_shape": "autotuned: %s" % json.dumps(
+                               [{k: r[k] for k in ("sweep_variant", "lanes_per_walker", "walkers_per_block",
+                                                   "ms_per_launch")} for r in tune_res]) if tune_res else
+                           "automatic (sweep_variant %d)" % i1["sweep_variant"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (3 * (SPF // SPE) + 1), "clocks": clocks,
                 "solve_state": {"sweep_clock": i1["sweep_clock"], "windows_done": i1["windows_done"]}}
@@ -710,6 +721,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true", help="time the sweep launch shapes first (rewl_autotune)")
     ap.add_argument("--requests", type=int, default=192, help="served-stream: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="served-stream: Poisson arrivals per second (0 = all at once)")
     ap.add_argument("--slots", type=int, default=96, help="served-stream: request slots")

@@ -278,6 +278,32 @@ typedef struct {
 rewl_status rewl_get_state(rewl_handle h, rewl_state* st);
 
 /*
+ * rewl_autotune -- picks the sweep kernel's launch shape for one problem by
+ * timing candidates on the problem itself: the ring form (32 lanes and a
+ * producer warp per walker) and the chain form with 32, 16, 8, 4 and 2 lanes
+ * per walker (walkers per CTA as rewl_create chooses).  Each candidate is a
+ * fresh rewl_create with the given arguments, one warm-up block, then `sweeps`
+ * sweeps timed with CUDA events around every sweep launch.  All candidates
+ * compute the same bits.  results: caller array of `capacity` entries, one per
+ * candidate tried (*n_results); *best: `params` (or the defaults) with
+ * sweep_variant, lanes_per_walker and walkers_per_block of the fastest, ready
+ * for rewl_create.  Errors: REWL_EINVAL (arguments, sweeps not a multiple of
+ * sweeps_per_exchange, no candidate ran); a candidate's own failure is in its
+ * result's status.
+ */
+typedef struct {
+  int32_t sweep_variant, lanes_per_walker, walkers_per_block;
+  int32_t status;           /* rewl_status of the candidate's run */
+  double ms_per_launch;     /* mean device time of one sweep launch (sweeps_per_exchange sweeps) */
+  double attempts_per_s;    /* trials per second of sweep-kernel time */
+} rewl_tune_result;
+
+rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice* lattice, const int8_t* couplings,
+                          int32_t windows, double overlap, int32_t walkers_per_window, double flatness,
+                          double lnf_final, uint64_t seed, const rewl_params* params, int32_t sweeps,
+                          rewl_tune_result* results, int32_t capacity, int32_t* n_results, rewl_params* best);
+
+/*
  * rewl_plan_windows -- the run-time balanced partition of Fig. 1b: windows
  * sized so that each finishes its first WL iteration after about the same
  * number of sweeps, estimated from a pre-run (the speed-up paragraph).  The

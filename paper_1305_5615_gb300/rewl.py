@@ -27,7 +27,7 @@ EXPORTED = ["rewl_params_default", "rewl_create", "rewl_step", "rewl_get_lng", "
             "rewl_get_info", "rewl_get_state", "rewl_set_state", "rewl_destroy", "rewl_status_str",
             "rewl_last_error", "rewl_sweep_noalloc", "rewl_server_create", "rewl_server_submit", "rewl_server_run",
             "rewl_server_poll", "rewl_server_result", "rewl_server_cancel", "rewl_server_destroy", "rewl_thermo",
-            "rewl_thermo_jackknife", "rewl_plan_windows"]
+            "rewl_thermo_jackknife", "rewl_plan_windows", "rewl_autotune"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 
@@ -91,6 +91,12 @@ class rewl_server_stats(ctypes.Structure):
     _fields_ = [("running", ctypes.c_int32), ("queued", ctypes.c_int32), ("finished", ctypes.c_int32),
                 ("failed", ctypes.c_int32), ("rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("device_bytes_in_use", ctypes.c_int64)]
+
+
+class rewl_tune_result(ctypes.Structure):
+    _fields_ = [("sweep_variant", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
+                ("walkers_per_block", ctypes.c_int32), ("status", ctypes.c_int32), ("ms_per_launch", ctypes.c_double),
+                ("attempts_per_s", ctypes.c_double)]
 
 
 class rewl_state(ctypes.Structure):
@@ -169,6 +175,10 @@ def load(build_if_missing=True):
     L.rewl_thermo_jackknife.restype = ctypes.c_int
     L.rewl_plan_windows.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P, P]
     L.rewl_plan_windows.restype = ctypes.c_int
+    L.rewl_autotune.argtypes = [P, P, P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_uint64, P, ctypes.c_int32, P, ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_int32), P]
+    L.rewl_autotune.restype = ctypes.c_int
     L.rewl_thermo.restype = ctypes.c_int
     _lib = L
     return L
@@ -275,6 +285,28 @@ def rewl_thermo(lng, e_min, e_step, temperatures):
     out = np.zeros((len(T), 5), np.float64)
     _check(load().rewl_thermo(_p(g), len(g), e_min, e_step, _p(T), len(T), _p(out)), "rewl_thermo")
     return out
+
+
+def rewl_autotune(model, L, windows, overlap, walkers_per_window, flatness, lnf_final, seed, q=2, couplings=None,
+                  sweeps=200, sweeps_per_exchange=100, sweeps_per_flat_check=1000):
+    """Times the sweep launch shapes on this problem (rewl_autotune): returns
+    (the keyword arguments of the fastest for REWL(), the list of results)."""
+    if isinstance(model, str):
+        model = MODELS[model]
+    p = rewl_params_default()
+    p.sweeps_per_exchange, p.sweeps_per_flat_check = sweeps_per_exchange, sweeps_per_flat_check
+    cpl = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
+    res = (rewl_tune_result * 8)()
+    n = ctypes.c_int32()
+    best = rewl_params()
+    dim = 3 if model == EA_PM_J_3D else 2
+    _check(load().rewl_autotune(ctypes.byref(rewl_model(model, q)), ctypes.byref(rewl_lattice(dim, L, L, 1)), _p(cpl),
+                                windows, overlap, walkers_per_window, flatness, lnf_final, ctypes.c_uint64(seed),
+                                ctypes.byref(p), sweeps, res, 8, ctypes.byref(n), ctypes.byref(best)), "rewl_autotune")
+    out = [{k: getattr(res[i], k) for k, _ in rewl_tune_result._fields_} for i in range(n.value)]
+    kw = {"sweep_variant": best.sweep_variant, "lanes_per_walker": best.lanes_per_walker,
+          "walkers_per_block": best.walkers_per_block}
+    return kw, out
 
 
 def rewl_plan_windows(first_iter_sweeps, pre_starts, pre_widths, n_bins, windows, overlap):

@@ -48,7 +48,7 @@ def test_create_fails_cleanly_without_a_suitable_device():
 
 
 STRUCTS = ("rewl_model", "rewl_lattice", "rewl_params", "rewl_info", "rewl_sweep_desc", "rewl_request",
-           "rewl_request_info", "rewl_server_stats", "rewl_state")
+           "rewl_request_info", "rewl_server_stats", "rewl_state", "rewl_tune_result")
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):
