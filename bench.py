@@ -75,10 +75,11 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def traffic_from_profile():
+def traffic_from_profile(workload, variant):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
-    if not os.path.exists(PROFILE_SUMMARY):
+    taken on the current kernel source, for this workload and sweep form
+    (the ring form on the default workload); else None."""
+    if workload != DEFAULT_WORKLOAD or variant != 2 or not os.path.exists(PROFILE_SUMMARY):
         return None
     kv = {}
     for line in open(PROFILE_SUMMARY):
@@ -184,14 +185,24 @@ def dist_setup():
     return world, rank, local
 
 
+ORACLE_TRIALS_PER_S = 2.5e7   # rough single-core oracle speed, to size the sample
+
+
 def oracle_rate(wl, seed, seconds):
     """Single-threaded oracle attempts/s on the same workload, for about
-    `seconds` of CPU work (whole exchange blocks; entry walk excluded)."""
+    `seconds` of CPU work (whole exchange blocks; entry walk excluded).  When
+    one block of the whole workload would take much longer than that, the
+    sample is the same lattice with 2 windows x 1 walker (the oracle's cost
+    per trial does not depend on the walker count).  Returns (rate, blocks,
+    seconds, walkers sampled)."""
     from oracle import OracleREWL
 
-    O = OracleREWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seed, q=wl["q"],
+    h, m = wl["h"], wl["m"]
+    if h * m * SPE * sites(wl) / ORACLE_TRIALS_PER_S > 2 * seconds:
+        h, m = 2, 1
+    O = OracleREWL(wl["model"], wl["L"], h, OVERLAP, m, FLATNESS, wl["lnf_final"], seed, q=wl["q"],
                    sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
-    n_walk = wl["h"] * wl["m"]
+    n_walk = h * m
     t0 = time.perf_counter()
     blocks = 0
     while True:
@@ -201,7 +212,7 @@ def oracle_rate(wl, seed, seconds):
         if el >= seconds:
             break
     attempts = blocks * SPE * O.N * n_walk
-    return attempts / el, blocks, el
+    return attempts / el, blocks, el, n_walk
 
 
 def run_reference(args, wl, world, rank):
@@ -318,7 +329,7 @@ def run_gb300(args, wl, world, rank, local):
         avg_s = sweep_ms / launches / 1e3
         achieved = att_per_launch * OPS_PER_ATTEMPT / avg_s / 1e12
         peak = N_SM * LANES_PER_SM_PER_CLK * f_max / 1e12
-        traffic = traffic_from_profile()
+        traffic = traffic_from_profile(args.workload, i1["sweep_variant"])
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_sweep", "avg_launch_ms": avg_s * 1e3,
                 "attempts_per_launch": att_per_launch, "ops_per_attempt": OPS_PER_ATTEMPT,
@@ -327,10 +338,13 @@ def run_gb300(args, wl, world, rank, local):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        rate, blocks, el = oracle_rate(wl, seed, args.cpu_seconds)
+        rate, blocks, el, n_walk = oracle_rate(wl, seed, args.cpu_seconds)
+        what = ("the same workload" if n_walk == wl["h"] * wl["m"] else
+                "the same lattice with 2 windows x 1 walker (a block of all %d walkers would take minutes)"
+                % (wl["h"] * wl["m"]))
         cpu = {"value": rate, "unit": "attempts/s", "cores": 1, "kind": "oracle",
-               "sample": "%d exchange blocks (%d sweeps) of the same workload, %.1f s, entry walk excluded"
-                         % (blocks, blocks * SPE, el)}
+               "sample": "%d exchange blocks (%d sweeps) of %s, %.1f s, entry walk excluded"
+                         % (blocks, blocks * SPE, what, el)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
@@ -414,6 +428,9 @@ def run_served(args, world, rank, local):
     from paper_1305_5615_gb300 import rewl
 
     reqs = served_requests(args.requests, args.seed)
+    if args.mix != "mixed":  # one shape only, e.g. "ising:32"
+        model, L = args.mix.split(":")
+        reqs = [dict(model=model, L=int(L), q=10 if model == "potts" else 2, seed=i) for i in range(len(reqs))]
     rng = np.random.default_rng(args.seed + 1)
     arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=len(reqs))) if args.rate > 0 else np.zeros(len(reqs))
     S = rewl.RewlServer(device_bytes=args.server_gb << 30, max_running=args.slots)
@@ -727,6 +744,7 @@ def main():
     ap.add_argument("--slots", type=int, default=96, help="served-stream: request slots")
     ap.add_argument("--server-gb", type=int, default=64, help="served-stream: device-memory budget in GiB")
     ap.add_argument("--plain-check", type=int, default=3, help="served-stream: solve this many plain in full")
+    ap.add_argument("--mix", default="mixed", help="served-stream: 'mixed', or one shape as model:L (e.g. ising:32)")
     ap.add_argument("--served-timeout", type=float, default=1200.0, help="served-stream: stop after this many seconds")
     ap.add_argument("--base-workload", default="potts-q10-L32-h32-m16", choices=sorted(WORKLOADS),
                     help="windows-balance, time-to-dos: the problem")
