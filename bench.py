@@ -188,58 +188,163 @@ def dist_setup():
 ORACLE_TRIALS_PER_S = 2.5e7   # rough single-core oracle speed, to size the sample
 
 
-def oracle_rate(wl, seed, seconds):
-    """Single-threaded oracle attempts/s on the same workload, for about
-    `seconds` of CPU work (whole exchange blocks; entry walk excluded).  When
-    one block of the whole workload would take much longer than that, the
-    sample is the same lattice with 2 windows x 1 walker (the oracle's cost
-    per trial does not depend on the walker count).  Returns (rate, blocks,
-    seconds, walkers sampled)."""
-    from oracle import OracleREWL
-
+def _oracle_sample_shape(wl, seconds):
+    """Windows and walkers of the oracle's timing sample: the workload itself,
+    or the same lattice with 2 windows x 1 walker when one exchange block of
+    the whole workload would take much longer than `seconds` (the oracle's
+    cost per trial does not depend on the walker count)."""
     h, m = wl["h"], wl["m"]
     if h * m * SPE * sites(wl) / ORACLE_TRIALS_PER_S > 2 * seconds:
         h, m = 2, 1
+    return h, m
+
+
+def _oracle_blocks(wl, h, m, seed, seconds, barrier=None):
+    """Creates one oracle solve (entry walk untimed), optionally waits at
+    `barrier`, then runs whole exchange blocks for about `seconds`.
+    Returns (attempts, seconds, blocks)."""
+    from oracle import OracleREWL
+
     O = OracleREWL(wl["model"], wl["L"], h, OVERLAP, m, FLATNESS, wl["lnf_final"], seed, q=wl["q"],
                    sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
-    n_walk = h * m
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
-    blocks = 0
+    blocks, att = 0, 0
     while True:
+        active = m * sum(1 for d in O.windows()["done"] if not d)  # walkers of windows still running
+        if active == 0:
+            break
         O.run_blocks(1)
         blocks += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
+        att += active * SPE * O.N
+        if time.perf_counter() - t0 >= seconds:
             break
-    attempts = blocks * SPE * O.N * n_walk
-    return attempts / el, blocks, el, n_walk
+    return att, time.perf_counter() - t0, blocks
+
+
+def oracle_rate(wl, seed, seconds):
+    """Single-threaded oracle attempts/s on the workload, for about `seconds`
+    of CPU work (whole exchange blocks; entry walk excluded).  Returns (rate,
+    blocks, seconds, walkers sampled)."""
+    h, m = _oracle_sample_shape(wl, seconds)
+    att, el, blocks = _oracle_blocks(wl, h, m, seed, seconds)
+    return att / el, blocks, el, h * m
+
+
+def host_cores():
+    return os.cpu_count() or 1
+
+
+def oracle_rate_all_cores(wl, seed, seconds):
+    """P = host_cores() independent oracle solves (seeds seed .. seed+P-1),
+    one thread each, run at the same time: aggregate attempts/s.  The
+    oracle's C calls release the interpreter lock, so the threads run on P
+    cores; the oracle itself is unchanged.  All solves start their timed
+    blocks together (a barrier after the untimed entry walks); the aggregate
+    is the sum of the attempts over the longest thread's time.  Returns
+    (rate, P, seconds, walkers sampled per solve)."""
+    P = host_cores()
+    h, m = _oracle_sample_shape(wl, seconds)
+    bar = threading.Barrier(P)
+    res = [None] * P
+
+    def work(k):
+        res[k] = _oracle_blocks(wl, h, m, seed + k, seconds, bar)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(P)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    att = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return att / el, P, el, h * m
+
+
+def oracle_time_to_dos(wl, seeds, sweeps, limit_s):
+    """The oracle's own time to the converged ln g, seed by seed.  Each
+    seed's sweep count is known from the GPU solve (the trajectories are the
+    same), so the oracle's time is first estimated from its measured rate;
+    if every seed fits in `limit_s`, all seeds are solved by the oracle in
+    full, host_cores() at a time in threads, each timed from create to done
+    (and its sweep count checked); otherwise the per-seed times are the
+    estimate, and the result says so."""
+    import concurrent.futures
+
+    rate, _, _, _ = oracle_rate(wl, seeds[0], 3.0)
+    per_trial = 1.0 / rate
+    est = [sw * wl["h"] * wl["m"] * sites(wl) * per_trial for sw in sweeps]
+    out = {"single_core_attempts_per_s": rate, "estimated_s": est}
+    if max(est) > limit_s:
+        out["measured"] = False
+        out["per_seed_s"] = est
+        out["how"] = ("estimated, an upper bound: GPU sweep count of each seed x every walker x oracle seconds "
+                      "per trial (measured single-threaded; windows that finish early stop costing, which the "
+                      "bound ignores); a full oracle solve would exceed %.0f s" % limit_s)
+        return out
+    from oracle import OracleREWL
+
+    def solve(sd):
+        t0 = time.perf_counter()
+        O = OracleREWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd, q=wl["q"],
+                       sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
+        while not O.run_blocks(SPF // SPE):
+            pass
+        el = time.perf_counter() - t0
+        return el, O.info()["sweep_clock"], O.joined_lng()
+
+    P = min(host_cores(), len(seeds))
+    t0 = time.perf_counter()
+    with concurrent.futures.ThreadPoolExecutor(max_workers=P) as ex:
+        res = list(ex.map(solve, seeds))
+    out.update({"measured": True, "threads": P, "wall_s": time.perf_counter() - t0,
+                "per_seed_s": [r[0] for r in res], "sweeps": [int(r[1]) for r in res],
+                "how": "every seed solved by the oracle in full, %d at a time (one thread each)" % P})
+    out["_lng"] = [r[2] for r in res]
+    return out
 
 
 def run_reference(args, wl, world, rank):
-    """The reference arm: the plain CPU oracle on the machine's host cores."""
+    """The reference arm: the plain CPU oracle on the machine's host cores, as P =
+    host_cores() independent solves (one thread each, seeds 0 .. P-1) that
+    run their exchange blocks at the same time.  A step is one exchange block
+    (100 sweeps) of every solve; the step's time is the slowest solve's."""
     if rank != 0:
         return
     from oracle import OracleREWL
 
-    O = OracleREWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], 0, q=wl["q"],
-                   sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF)
-    per_step = SPE * sites(wl) * wl["h"] * wl["m"]
-    for _ in range(args.warmup):
-        O.run_blocks(1)
-    times = []
-    for _ in range(args.steps):
+    P = host_cores()
+    h, m = _oracle_sample_shape(wl, 2.0)
+    per_step = SPE * sites(wl) * h * m
+    solves = [OracleREWL(wl["model"], wl["L"], h, OVERLAP, m, FLATNESS, wl["lnf_final"], k, q=wl["q"],
+                         sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF) for k in range(P)]
+
+    def one_step():
+        th = [threading.Thread(target=O.run_blocks, args=(1,)) for O in solves]
         t0 = time.perf_counter()
-        O.run_blocks(1)
-        times.append(time.perf_counter() - t0)
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one_step()
+    times = [one_step() for _ in range(args.steps)]
     tot = sum(times)
-    value = args.steps * per_step / tot
-    sample = ("%d blocks of %d sweeps of the %s workload (%d walkers x %d sites) per step = 1/%d of a "
-              "flatness period" % (1, SPE, args.workload, wl["h"] * wl["m"], sites(wl), SPF // SPE))
+    value = args.steps * P * per_step / tot
+    what = ("the %s workload (%d walkers x %d sites)" % (args.workload, h * m, sites(wl)) if h * m == wl["h"] * wl["m"]
+            else "the %s lattice with 2 windows x 1 walker (a block of all %d walkers would take minutes)"
+            % (args.workload, wl["h"] * wl["m"]))
+    sample = ("per step, one block of %d sweeps of %s in each of %d independent oracle solves run at once "
+              "(one thread each; seeds 0..%d)" % (SPE, what, P, P - 1))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "step": "one exchange block (100 sweeps)"},
-            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": args.workload, "desc": wl["desc"],
+                       "step": "one exchange block (100 sweeps) of each of %d oracle solves" % P},
+            "cpu_baseline": {"value": value, "unit": "attempts/s", "cores": P, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -345,6 +450,12 @@ def run_gb300(args, wl, world, rank, local):
         cpu = {"value": rate, "unit": "attempts/s", "cores": 1, "kind": "oracle",
                "sample": "%d exchange blocks (%d sweeps) of %s, %.1f s, entry walk excluded"
                          % (blocks, blocks * SPE, what, el)}
+        if args.cpu_all_cores:
+            rate_p, P, el_p, _ = oracle_rate_all_cores(wl, seed, args.cpu_seconds)
+            cpu["all_cores"] = {"value": rate_p, "unit": "attempts/s", "cores": P, "kind": "oracle",
+                                "sample": "%d independent oracle solves of %s (seeds %d..%d), one thread each, "
+                                          "%.1f s of whole exchange blocks at the same time" % (
+                                              P, what, seed, seed + P - 1, el_p)}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
@@ -665,6 +776,23 @@ def run_time_to_dos(args, world, rank, local):
     sps = float(np.mean(per_sweep)) if per_sweep else None
     svc = [plain[k] if k < len(plain) else sps * sweeps[k] for k in range(len(seeds))]
     queued = list(np.cumsum(svc))          # all submitted at t = 0, solved one after another
+    orc = None
+    if rank == 0 and not args.no_cpu:
+        orc = oracle_time_to_dos(wl, seeds, sweeps, args.tdos_oracle_limit)
+        lngs = orc.pop("_lng", None)
+        if lngs is not None:
+            dev = []
+            for k, g_o in enumerate(lngs):
+                g_s = S.result(ids[k])[0]
+                fin = np.isfinite(g_o)
+                same_support = bool(np.array_equal(np.isfinite(g_s), fin))
+                dev.append(float(np.abs(g_s[fin] - g_o[fin]).max()) if same_support else None)
+            orc["sweeps_equal_gpu"] = orc["sweeps"] == [int(s) for s in sweeps]
+            orc["max_abs_lng_diff_vs_gpu"] = dev
+        orc["p50_s"] = float(np.percentile(orc["per_seed_s"], 50))
+        orc["p99_s"] = float(np.percentile(orc["per_seed_s"], 99))
+        orc["queued_one_core_p50_s"] = float(np.percentile(np.cumsum(orc["per_seed_s"]), 50))
+        orc["queued_one_core_p99_s"] = float(np.percentile(np.cumsum(orc["per_seed_s"]), 99))
     if rank == 0:
         print(json.dumps({"metric": "time to converged ln g (ln f_final), p50/p99 over seeds, served vs plain",
                           "value": float(np.percentile(served, 50)), "unit": "s (served p50)", "n_gpus": world,
@@ -679,7 +807,8 @@ def run_time_to_dos(args, world, rank, local):
                                     "service_p99_s": float(np.percentile(svc, 99)),
                                     "queued_p50_s": float(np.percentile(queued, 50)),
                                     "queued_p99_s": float(np.percentile(queued, 99)),
-                                    "bit_identical_to_served": bits}}), flush=True)
+                                    "bit_identical_to_served": bits},
+                          "oracle": orc}), flush=True)
 
 
 def run_glass_e0(args, world, rank, local):
@@ -738,6 +867,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-all-cores", type=int, default=1,
+                    help="also time one oracle solve per host core at the same time (0 = single core only)")
+    ap.add_argument("--tdos-oracle-limit", type=float, default=300.0,
+                    help="time-to-dos: solve the seeds with the oracle in full if each takes less than this (s)")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch shapes first (rewl_autotune)")
     ap.add_argument("--requests", type=int, default=192, help="served-stream: number of requests")
     ap.add_argument("--rate", type=float, default=0.0, help="served-stream: Poisson arrivals per second (0 = all at once)")

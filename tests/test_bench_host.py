@@ -1,0 +1,38 @@
+"""Host-side logic of bench.py that needs no GPU: the oracle timing samples
+and the reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_sample_shape_shrinks_only_for_large_workloads():
+    assert bench._oracle_sample_shape(bench.WORKLOADS["ising-L32-h16-m4"], 12.0) == (16, 4)
+    assert bench._oracle_sample_shape(bench.WORKLOADS["ising-L8-h4-m2"], 12.0) == (4, 2)
+    assert bench._oracle_sample_shape(bench.WORKLOADS["ising-L128-h128-m32"], 12.0) == (2, 1)
+
+
+def test_oracle_sample_stops_at_convergence():
+    """Ising 8 x 8, 4 windows x 2 walkers, seed 0 converges after 63000 sweeps
+    (the oracle's own run): a sample with no time limit runs exactly those
+    630 blocks and counts at most every walker's attempts in each."""
+    wl = bench.WORKLOADS["ising-L8-h4-m2"]
+    att, el, blocks = bench._oracle_blocks(wl, 4, 2, 0, 1e9)
+    assert blocks == 630
+    assert 0 < att <= blocks * bench.SPE * 64 * 8
+    assert att < blocks * bench.SPE * 64 * 8     # windows that finish early stop counting
+
+
+def test_reference_arm_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3", "--workload", "ising-L8-h4-m2"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "attempts/s" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == bench.host_cores() and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
