@@ -762,16 +762,31 @@ def run_time_to_dos(args, world, rank, local):
         inf = S.poll(rid)
         served.append(inf["latency_ms"] / 1e3)
         sweeps.append(inf["sweeps"])
-    plain, per_sweep, bits = [], [], []
+    tuned, tune_res = {}, None
+    if args.autotune:
+        tuned, tune_res = rewl.rewl_autotune(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS,
+                                             wl["lnf_final"], args.seed, q=wl["q"], sweeps=SPF)
+    plain, per_sweep, bits, secondary = [], [], [], None
     for k, sd in enumerate(seeds[:args.tdos_plain]):
         t1 = time.perf_counter()
-        D = rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd, q=wl["q"])
+        D = rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd, q=wl["q"],
+                      mode=rewl.MODE_GRAPH if args.mode == "graph" else rewl.MODE_PLAIN, **tuned)
         D.step(0)
         g, _, _ = D.lng()
         el = time.perf_counter() - t1
         plain.append(el)
         per_sweep.append(el / D.info["sweep_clock"])
         bits.append(bool(np.array_equal(g.view(np.uint64), S.result(ids[k])[0].view(np.uint64))))
+        if k == 0:
+            ds = D.state()
+            tried = ds["x_tried"][:-1].astype(np.float64)
+            secondary = {"seed": sd, "sweeps_to_converge": int(ds["sweep_clock"]),
+                         "iterations_per_window": [int(x) for x in ds["iteration"]],
+                         "exchange_acceptance_per_pair": [float(a) / t if t else None for a, t in
+                                                          zip(ds["x_accepted"][:-1].astype(np.float64), tried)],
+                         "exchange_rounds": int(ds["exchange_rounds"]),
+                         "replica_round_trips": int(ds["rep_trips"].sum()),
+                         "wl_acceptance": float(ds["wl_accept"].sum()) / float(D.info["attempts"])}
         D.close()
     sps = float(np.mean(per_sweep)) if per_sweep else None
     svc = [plain[k] if k < len(plain) else sps * sweeps[k] for k in range(len(seeds))]
@@ -798,7 +813,10 @@ def run_time_to_dos(args, world, rank, local):
                           "value": float(np.percentile(served, 50)), "unit": "s (served p50)", "n_gpus": world,
                           "higher_is_better": False, "dtype": "f64", "data": "synthetic",
                           "config": {"workload": "time-to-dos", "base": args.base_workload, "desc": wl["desc"],
-                                     "seeds": seeds},
+                                     "seeds": seeds, "plain_mode": args.mode,
+                                     "plain_launch_shape": ("autotuned: %s" % json.dumps(
+                                         [{k: r[k] for k in ("sweep_variant", "lanes_per_walker", "ms_per_launch")}
+                                          for r in tune_res]) if tune_res else "automatic")},
                           "served": {"wall_s": t_served, "p50_s": float(np.percentile(served, 50)),
                                      "p99_s": float(np.percentile(served, 99)), "per_seed_s": served,
                                      "sweeps": sweeps, "attempts_per_s": st["attempts"] / t_served},
@@ -808,7 +826,7 @@ def run_time_to_dos(args, world, rank, local):
                                     "queued_p50_s": float(np.percentile(queued, 50)),
                                     "queued_p99_s": float(np.percentile(queued, 99)),
                                     "bit_identical_to_served": bits},
-                          "oracle": orc}), flush=True)
+                          "secondary": secondary, "oracle": orc}), flush=True)
 
 
 def run_glass_e0(args, world, rank, local):
