@@ -309,6 +309,7 @@ struct TrialEval {
   int dbin;          // (E_new - E_old) / e_step
   uint32_t widx;     // lattice word (shared-memory index) the move writes
   uint32_t wmask;    // Ising / +-J: bit to flip;  Potts: nibble shift (low 8 bits) | new value << 8
+  uint32_t delta;    // the move as an XOR on the word: Ising / +-J the bit; Potts (old ^ new value) << shift
 };
 
 template <int MODEL>
@@ -335,6 +336,7 @@ __device__ __forceinline__ TrialEval<MODEL> eval_trial(const Problem& P, const u
     t.dbin = sat - 3;  // dE = 4 * satisfied - 12
     t.widx = (uint32_t)((row * Wr + (x >> 5)) * wpb + lw);
     t.wmask = 1u << (x & 31);
+    t.delta = t.wmask;
   } else if constexpr (MODEL == kPotts) {
     const uint32_t v = potts_val(s_lat, wpb, lw, Wr, x, y);
     uint32_t nv = v + 1u + pv;
@@ -345,6 +347,7 @@ __device__ __forceinline__ TrialEval<MODEL> eval_trial(const Problem& P, const u
              (int)(n3 == nv) - (int)(n4 == nv);
     t.widx = (uint32_t)((y * Wr + (x >> 3)) * wpb + lw);
     t.wmask = (uint32_t)((x & 7) * 4) | (nv << 8);
+    t.delta = (v ^ nv) << ((x & 7) * 4);
   } else {
     const uint32_t c = spin_bit(s_lat, wpb, lw, Wr, x, y);
     const uint32_t nr = spin_bit(s_lat, wpb, lw, Wr, xr, y), nl = spin_bit(s_lat, wpb, lw, Wr, xl, y);
@@ -361,6 +364,7 @@ __device__ __forceinline__ TrialEval<MODEL> eval_trial(const Problem& P, const u
     t.dbin = sat - 2;  // dE = 4 * satisfied - 8
     t.widx = (uint32_t)((y * Wr + (x >> 5)) * wpb + lw);
     t.wmask = 1u << (x & 31);
+    t.delta = t.wmask;
   }
   return t;
 }
@@ -383,6 +387,22 @@ struct StagedTrial {
   uint32_t wmask;  // Ising / +-J: bit to flip;  Potts: nibble shift | new value << 8
   int64_t thr;     // ln u in units of 2^-40 (float log; see kGuardFx)
 };
+
+// The chain forms split a staged trial in two: what the sequential step reads
+// for every trial (16 bytes, one shared-memory load) and the move itself, which
+// the sequential step does not touch: accepted moves are written to the
+// configuration by their own lanes after the group (an XOR per move), except
+// where a later trial of the group needs the configuration they leave.
+struct __align__(16) HotTrial {
+  int64_t thr;     // ln u in units of 2^-40
+  uint32_t pk;     // dbin + 8 | pv << 8 | x << 16 | y << 24
+  uint32_t mask;   // earlier trials of the group whose site lies in this trial's neighbourhood
+};
+struct __align__(8) ColdTrial {
+  uint32_t widx;   // lattice word the move writes
+  uint32_t delta;  // the move as an XOR on that word
+};
+static_assert(sizeof(HotTrial) + sizeof(ColdTrial) == sizeof(StagedTrial), "staging size");
 
 template <int MODEL, int G>
 __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, SweepLaunch A) {
@@ -670,8 +690,9 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   PreTrial* s_ring = reinterpret_cast<PreTrial*>(smem);                                  // [kRingSlots][32]
   uint64_t* s_full = reinterpret_cast<uint64_t*>(s_ring + kRingSlots * 32);              // [kRingSlots]
   uint64_t* s_empty = s_full + kRingSlots;                                               // [kRingSlots]
-  StagedTrial* s_stage = reinterpret_cast<StagedTrial*>(smem + (RING ? kRingBytes : 0));  // [wpb][G]
-  int64_t* s_fx = reinterpret_cast<int64_t*>(s_stage + (G > 1 ? (size_t)wpb * G : 0));  // [wpad][wpb]
+  HotTrial* s_hot = reinterpret_cast<HotTrial*>(smem + (RING ? kRingBytes : 0));         // [wpb][G]
+  ColdTrial* s_cold = reinterpret_cast<ColdTrial*>(s_hot + (G > 1 ? (size_t)wpb * G : 0));  // [wpb][G]
+  int64_t* s_fx = reinterpret_cast<int64_t*>(s_cold + (G > 1 ? (size_t)wpb * G : 0));      // [wpad][wpb]
   uint32_t* s_lat = reinterpret_cast<uint32_t*>(s_fx + (size_t)wpad * wpb);
   uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
   const int nthr = blockDim.x;
@@ -737,7 +758,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     const uint32_t gm = group_mask<G>();
     const int L = P.L, w = window_width(P, S, a);  // the window test; P.w is the layout stride
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
-    StagedTrial* my_stage = s_stage + (size_t)lw * G;
+    HotTrial* my_hot = s_hot + (size_t)lw * G;
+    ColdTrial* my_cold = s_cold + (size_t)lw * G;
 
     const PreTrial* my_pre = pre ? pre + (size_t)W * pre_stride : nullptr;
     PreTrial nxt_pre{0u, 0u, 0};
@@ -745,7 +767,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     long long deadline = 0;
     if constexpr (RING) deadline = __shfl_sync(0xffffffffu, clock64(), 0) + kRingWaitCycles;
     for (uint32_t base = 0; base < n_att; base += G) {
-      StagedTrial tr;
+      HotTrial tr;
+      ColdTrial mv_own;  // this lane's move, written after the group if accepted
       {
         int x, y;
         uint32_t pv, M = 0;
@@ -782,19 +805,23 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
         const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
         tr.pk = (uint32_t)(ev.dbin + 8) | (pv << 8) | (pk << 16);
         tr.mask = M;
-        tr.widx = ev.widx;
-        tr.wmask = ev.wmask;
-        if constexpr (G > 1) my_stage[lane] = tr;
+        mv_own.widx = ev.widx;
+        mv_own.delta = ev.delta;
+        if constexpr (G > 1) {
+          my_hot[lane] = tr;
+          my_cold[lane] = mv_own;
+        }
       }
       if constexpr (G > 1) __syncwarp(gm);
 
+      uint32_t pending = 0;  // accepted trials of the group whose move is not written yet
       if (lane == 0) {
         const int n_here = (int)min((uint32_t)G, n_att - base);
-        uint32_t accm = 0;
-        StagedTrial cc = tr, cn = tr;  // trial j and trial j+1
+        uint32_t accm = 0, written = 0;
+        HotTrial cc = tr, cn = tr;  // trial j and trial j+1
         if constexpr (G > 1) {
-          cc = my_stage[0];
-          cn = my_stage[n_here > 1 ? 1 : 0];
+          cc = my_hot[0];
+          cn = my_hot[n_here > 1 ? 1 : 0];
         }
         int dj = (int)(cc.pk & 0xffu) - 8;
         int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of trial 0's target bin
@@ -806,13 +833,12 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           for (; j < n_here; ++j) {
             // loads that do not depend on trial j's outcome first (shared-memory operations
             // issue in order and must not queue behind trial j's stores)
-            StagedTrial cnn = cn;
-            if constexpr (G > 1) cnn = my_stage[min(j + 2, n_here - 1)];
+            HotTrial cnn = cn;
+            if constexpr (G > 1) cnn = my_hot[min(j + 2, n_here - 1)];
             const int dn = (int)(cn.pk & 0xffu) - 8;
             const int bn = bin + dj;
             const int64_t cand_stay = fxp[(bin + dn) * wpb];  // trial j+1's target if trial j stays
             const int64_t cand_move = fxp[(bn + dn) * wpb];   // trial j+1's target if trial j moves
-            const uint32_t word = s_lat[cc.widx];
             // accept iff (shadow_old - shadow_new) - ln u > guard; reject iff < -guard
             const bool inwin = (unsigned)bn < (unsigned)w;
             const int64_t lim_acc = fx_cur - cc.thr - kGuardFx;
@@ -821,14 +847,6 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
             const bool band = dj != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
             if (band || (accm & cc.mask) != 0u) break;
             const bool mv = acc && dj != 0;
-            uint32_t nword;
-            if constexpr (MODEL == kPotts) {
-              const uint32_t sh = cc.wmask & 0xffu, nv = cc.wmask >> 8;
-              nword = (word & ~(15u << sh)) | (nv << sh);
-            } else {
-              nword = word ^ cc.wmask;
-            }
-            s_lat[cc.widx] = acc ? nword : word;
             if (mv) fxp[bin * wpb] = fx_cur;  // write back the shadow of the bin left
             accm |= (uint32_t)acc << j;
             const int64_t fwd = (dn == -dj) ? fx_cur : cand_move;  // trial j+1 targets the bin just left
@@ -841,15 +859,21 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           }
           if (j >= n_here) break;
           // ---- slow path for trial j: re-evaluate on the current configuration when an
-          //      accepted earlier trial of the group touched its neighbourhood, and decide
-          //      exactly in FP64 when the fast test falls in the guard band
-          uint32_t widx = cc.widx, wmask = cc.wmask;
-          if ((accm & cc.mask) != 0u) {
-            const TrialEval<MODEL> e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cc.pk >> 16) & 0xffu),
-                                                         (int)(cc.pk >> 24), (cc.pk >> 8) & 0xffu);
+          //      accepted earlier trial of the group touched its neighbourhood (first writing
+          //      those moves), and decide exactly in FP64 when the fast test falls in the
+          //      guard band
+          const uint32_t hit = accm & cc.mask;
+          TrialEval<MODEL> e2{};
+          if (hit != 0u) {
+            if constexpr (G > 1)
+              for (uint32_t p = hit & ~written; p != 0u; p &= p - 1u) {
+                const ColdTrial c = my_cold[__ffs(p) - 1];
+                s_lat[c.widx] ^= c.delta;
+              }
+            written |= hit;
+            e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cc.pk >> 16) & 0xffu), (int)(cc.pk >> 24),
+                                   (cc.pk >> 8) & 0xffu);
             dj = e2.dbin;
-            widx = e2.widx;
-            wmask = e2.wmask;
           }
           const int bn = bin + dj;
           const bool inwin = (unsigned)bn < (unsigned)w;
@@ -863,13 +887,9 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
             ++n_exact;
           }
           const bool mv = acc && dj != 0;
-          if (acc) {
-            if constexpr (MODEL == kPotts) {
-              const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
-              s_lat[widx] = (s_lat[widx] & ~(15u << sh)) | (nv << sh);
-            } else {
-              s_lat[widx] ^= wmask;
-            }
+          if (acc && hit != 0u) {  // a re-evaluated move is written at once
+            s_lat[e2.widx] ^= e2.delta;
+            written |= 1u << j;
           }
           if (mv) fxp[bin * wpb] = fx_cur;
           accm |= (uint32_t)acc << j;
@@ -878,14 +898,23 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           ++j;
           if (j < n_here) {  // re-prime the fast loop: trial j+1 and j+2, and trial j's target shadow
             cc = cn;
-            if constexpr (G > 1) cn = my_stage[min(j + 1, n_here - 1)];
+            if constexpr (G > 1) cn = my_hot[min(j + 1, n_here - 1)];
             dj = (int)(cc.pk & 0xffu) - 8;
             fxn = fxp[(bin + dj) * wpb];
           }
         }
         n_acc += (uint64_t)__popc(accm);
+        pending = accm & ~written;
       }
-      if constexpr (G > 1) __syncwarp(gm);
+      // every lane writes its own trial's move if it was accepted and is not written yet; two such
+      // moves never touch the same site (the later one would have met the earlier in its mask)
+      if constexpr (G > 1) {
+        pending = __shfl_sync(gm, pending, 0, G);
+        if ((pending >> lane) & 1u) atomicXor(&s_lat[mv_own.widx], mv_own.delta);
+        __syncwarp(gm);
+      } else {
+        if (pending & 1u) s_lat[mv_own.widx] ^= mv_own.delta;
+      }
     }
     if (lane == 0) {
       fxp[bin * wpb] = fx_cur;
@@ -1384,7 +1413,7 @@ static cudaError_t launch_sweep_m(int G, const Problem& P, const DevState& S, co
 size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
   size_t b = variant == kSweepStaged ? (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4)
                                      : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
-  if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);
+  if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);  // the staged form's trials, or HotTrial + ColdTrial
   if (P.model == kEA || P.model == kEA3) b += (size_t)P.j_words * 4;
   if (variant == kSweepRing) b += kRingBytes;
   return b;
