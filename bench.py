@@ -75,6 +75,24 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+UBENCH_SUMMARY = os.path.join(ROOT, "profiles", "ubench_pipe_rates_and_wl_step_latency.txt")
+
+
+def isolated_step_cycles():
+    """Cycles per trial of the sequential WL step run on its own (the
+    microbenchmark's dependency chain on the int64 shadow), from the committed
+    summary; None if absent."""
+    if not os.path.exists(UBENCH_SUMMARY):
+        return None
+    for line in open(UBENCH_SUMMARY):
+        if line.startswith("int64 shadow, dependency chain only"):
+            try:
+                return float(line.split()[5])
+            except (IndexError, ValueError):
+                return None
+    return None
+
+
 def traffic_from_profile(workload, variant):
     """DRAM bytes per sweep launch from the committed ncu summary, if it was
     taken on the current kernel source, for this workload and sweep form
@@ -440,6 +458,14 @@ def run_gb300(args, wl, world, rank, local):
                 "attempts_per_launch": att_per_launch, "ops_per_attempt": OPS_PER_ATTEMPT,
                 "peak_basis": "152 SMs x 128 int lanes/clk x %.0f MHz (derived from unit counts and the maximum SM clock)" % (f_max / 1e6),
                 "sweep_share_of_step": sweep_ms / 1e3 / t_local if t_local > 0 else None}
+        iso = isolated_step_cycles()
+        f_run = (clocks or {}).get("sm_mhz") or f_max / 1e6
+        cyc = avg_s * f_run * 1e6 / (SPE * sites(wl))  # per trial of one walker (all walkers run at once)
+        if iso is not None and args.workload == DEFAULT_WORKLOAD:
+            roof["latency"] = {"unit": "clk/trial per walker", "kernel": cyc, "isolated_step": iso,
+                               "frac": iso / cyc, "sm_mhz": f_run,
+                               "basis": "the sequential WL step alone (dependency chain only), measured by "
+                                        "paper_1305_5615_gb300/ubench on the GB300"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -1,0 +1,3 @@
+from . import run
+
+print(run(), end="")

@@ -1,0 +1,302 @@
+// rates.cu -- microbenchmarks of the GB300 rates that bound the REWL sweep
+// kernel: FP64 add throughput and latency, double log and float logf
+// throughput, Philox4x32-10 throughput (the library's own generator),
+// shared-memory load and warp-shuffle latency, and the latency of the
+// sequential WL step itself (the chain bin -> shadow loads -> 64-bit compare
+// -> next bin) stripped of everything the sweep kernel does around it.
+//
+// Throughputs are per SM per clock: every block measures its own clock64
+// interval, all blocks of a launch are resident at once, and
+//   rate = (operations of the blocks on one SM) / (median block cycles).
+// Latencies are cycles per step of one dependent chain in one thread.
+//
+// Build and run: python -m paper_1305_5615_gb300.ubench
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../csrc/rewl_device.cuh"
+
+#define CK(x)                                                                      \
+  do {                                                                             \
+    cudaError_t e_ = (x);                                                          \
+    if (e_ != cudaSuccess) {                                                       \
+      std::fprintf(stderr, "%s:%d %s\n", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+      return 1;                                                                    \
+    }                                                                              \
+  } while (0)
+
+namespace {
+
+__device__ __forceinline__ void stamp(long long* cyc, long long t0) {
+  __syncthreads();
+  if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - t0;
+}
+
+// ---- FP64 add: 8 independent chains per thread
+__global__ void k_dadd_tput(double* out, long long* cyc, int iters) {
+  double a[8];
+  for (int k = 0; k < 8; ++k) a[k] = threadIdx.x + k;
+  const double c = 1e-9 * (blockIdx.x + 1);
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = a[k] + c;
+  stamp(cyc, t0);
+  double s = 0;
+  for (int k = 0; k < 8; ++k) s += a[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// ---- FP64 add: one dependent chain
+__global__ void k_dadd_lat(double* out, long long* cyc, int iters) {
+  double a = threadIdx.x;
+  const double c = 1e-9;
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) a = a + c;
+  cyc[0] = clock64() - t0;
+  out[0] = a;
+}
+
+// ---- double log / float logf on independent arguments
+__global__ void k_log_tput(double* out, long long* cyc, int iters) {
+  double x = 1.0 + 1e-3 * threadIdx.x, s = 0;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) {
+    s += log(x);
+    x += 0.5;
+  }
+  stamp(cyc, t0);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+__global__ void k_logf_tput(float* out, long long* cyc, int iters) {
+  float x0 = 1.0f + 1e-3f * threadIdx.x, x1 = x0 + 0.25f, x2 = x0 + 0.5f, x3 = x0 + 0.75f;
+  float s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) {
+    s0 += logf(x0);
+    s1 += logf(x1);
+    s2 += logf(x2);
+    s3 += logf(x3);
+    x0 += 1.0f;
+    x1 += 1.0f;
+    x2 += 1.0f;
+    x3 += 1.0f;
+  }
+  stamp(cyc, t0);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s0 + s1 + s2 + s3;
+}
+
+// ---- Philox4x32-10, the library's definition
+__global__ void k_philox_tput(uint32_t* out, long long* cyc, int iters) {
+  const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) {
+    const rewl::U4 r = rewl::philox10((uint32_t)i, 0u, id, 0u, 0x12345678u, 0x9abcdef0u);
+    acc ^= r.x ^ r.y ^ r.z ^ r.w;
+  }
+  stamp(cyc, t0);
+  out[id] = acc;
+}
+
+// ---- shared-memory load latency: pointer chase over a random cycle of 1024 words
+__global__ void k_lds_lat(int* out, long long* cyc, int iters) {
+  __shared__ int nxt[1024];
+  if (threadIdx.x == 0) {  // one cycle through all 1024 slots, stride 97 (odd, so a single cycle)
+    for (int i = 0; i < 1024; ++i) nxt[i] = (i + 97) & 1023;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  int p = 0;
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) p = nxt[p];
+  cyc[0] = clock64() - t0;
+  out[0] = p;
+}
+
+// ---- warp shuffle latency: a value passed around the warp
+__global__ void k_shfl_lat(int* out, long long* cyc, int iters) {
+  int v = threadIdx.x;
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) v = __shfl_sync(0xffffffffu, v, (threadIdx.x + 1) & 31) + 1;
+  if (threadIdx.x == 0) {
+    cyc[0] = clock64() - t0;
+    out[0] = v;
+  }
+}
+
+// ---- the sequential WL step on its own.  One walker per block (lane 0), a
+// window of W bins whose int64 shadow lives in shared memory with 4 guard
+// bins on each side, bin offsets in -2..2 and thresholds ln u * 2^40 made
+// beforehand.  variant 0: the dependency chain only (two candidate loads for
+// the next trial, the compare, the write-back of the bin left, the selects);
+// variant 1: plus the guard-band and conflict tests folded into a flag;
+// variant 2: the tests as a branch out of the loop (never taken here), as
+// the sweep kernel has them.  T = long long is the fixed-point shadow the
+// sweep kernel uses (units of 2^-40); T = double is the same step on FP64
+// ln g values, for comparison.
+constexpr int kSteps = 2048;  // inputs per pass, reused cyclically
+constexpr int kMaxW = 512;
+
+template <typename T>
+__device__ __forceinline__ T fx_scale(double v) {
+  if constexpr (sizeof(T) == 8 && T(0.5) == T(0)) return (T)(v * 1099511627776.0);
+  else return (T)v;
+}
+
+template <int VARIANT, typename T = long long>
+__global__ void k_chain(int W, int passes, long long* cyc, long long* out) {
+  __shared__ int s_d[kSteps];
+  __shared__ T s_thr[kSteps];
+  __shared__ unsigned s_mask[kSteps];
+  __shared__ T s_fx[kMaxW + 8];
+  for (int i = threadIdx.x; i < kSteps; i += blockDim.x) {
+    const rewl::U4 r = rewl::philox10((uint32_t)i, blockIdx.x, 7u, 0u, 0x2468aceu, 0x13579bdu);
+    const uint32_t k = rewl::scale32(r.x, 16u);  // 0, +-1 often; +-2 rarely (a 2D Ising walk's mix)
+    s_d[i] = k < 6 ? 0 : k < 10 ? 1 : k < 14 ? -1 : k < 15 ? 2 : -2;
+    const float u = ((float)(r.y >> 8) + 0.5f) * 0x1p-24f;
+    s_thr[i] = fx_scale<T>((double)logf(u));
+    s_mask[i] = 0u;
+  }
+  for (int b = threadIdx.x; b < W + 8; b += blockDim.x) {  // a smooth ln g-like shadow
+    const double x = (double)(b - 4) / W;
+    s_fx[b] = fx_scale<T>(200.0 * x * (1.0 - x) + 1.0);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  T* fxp = s_fx + 4;
+  const T lnf = fx_scale<T>(0x1p-10), guard = fx_scale<T>(0x1p-16);
+  int bin = W / 2, d = s_d[0];
+  T fx_cur = fxp[bin], fxn = fxp[bin + d];
+  unsigned accm = 0, bad = 0;
+  const long long t0 = clock64();
+  for (int p = 0; p < passes; ++p) {
+#pragma unroll 1
+    for (int j = 0; j < kSteps; ++j) {
+      const int dn = s_d[(j + 1) & (kSteps - 1)];
+      const T thr = s_thr[j];
+      const int bn = bin + d;
+      const T cs = fxp[bin + dn], cm = fxp[bn + dn];
+      const bool inwin = (unsigned)bn < (unsigned)W;
+      const T lim_acc = fx_cur - thr - guard;
+      const bool acc = d == 0 || (inwin && fxn < lim_acc);
+      if (VARIANT >= 1) {
+        const T lim_rej = fx_cur - thr + guard;
+        const bool band = d != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
+        const bool hit = band || (accm & s_mask[j]) != 0u;
+        if (VARIANT == 2) {
+          if (hit) {  // never taken: no conflicts are planted and the band is 3e-5 wide
+            bad += 1u + (unsigned)j;
+            break;
+          }
+        } else {
+          bad |= (unsigned)hit;
+        }
+        accm = (accm << 1) | (unsigned)acc;
+      }
+      const bool mv = acc && d != 0;
+      if (mv) fxp[bin] = fx_cur;
+      const T fwd = (dn == -d) ? fx_cur : cm;
+      fx_cur = (mv ? fxn : fx_cur) + lnf;
+      fxn = mv ? fwd : cs;
+      bin = mv ? bn : bin;
+      d = dn;
+    }
+  }
+  cyc[blockIdx.x] = clock64() - t0;
+  out[blockIdx.x] = (long long)fx_cur + bin + bad;
+}
+
+double median(std::vector<long long> v) {
+  std::sort(v.begin(), v.end());
+  return (double)v[v.size() / 2];
+}
+
+}  // namespace
+
+int main() {
+  int dev = 0, n_sm = 0, khz = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  CK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  std::printf("device SMs %d, max SM clock %.0f MHz\n", n_sm, khz / 1e3);
+  const int bps = 4, threads = 256, blocks = n_sm * bps;  // 1024 threads per SM, all resident
+  double* d_out = nullptr;
+  long long* d_cyc = nullptr;
+  CK(cudaMalloc(&d_out, sizeof(double) * blocks * threads));
+  CK(cudaMalloc(&d_cyc, sizeof(long long) * blocks));
+  std::vector<long long> cyc(blocks);
+  auto per_sm_clk = [&](double ops_per_block) {
+    cudaMemcpy(cyc.data(), d_cyc, sizeof(long long) * blocks, cudaMemcpyDeviceToHost);
+    return ops_per_block * bps / median(cyc);
+  };
+  long long one = 0;
+
+  const int it_add = 1 << 14;
+  k_dadd_tput<<<blocks, threads>>>(d_out, d_cyc, 16);
+  k_dadd_tput<<<blocks, threads>>>(d_out, d_cyc, it_add);
+  CK(cudaDeviceSynchronize());
+  std::printf("FP64 add, 8 independent chains per thread:  %8.3f lane-ops/clk/SM\n",
+              per_sm_clk((double)threads * 8 * it_add));
+  k_dadd_lat<<<1, 1>>>(d_out, d_cyc, 1 << 14);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&one, d_cyc, sizeof(long long), cudaMemcpyDeviceToHost));
+  std::printf("FP64 add dependent latency:                 %8.1f clk\n", (double)one / (1 << 14));
+
+  const int it_log = 1 << 9;
+  k_log_tput<<<blocks, threads>>>(d_out, d_cyc, it_log);
+  CK(cudaDeviceSynchronize());
+  std::printf("double log():                               %8.3f lane-ops/clk/SM\n",
+              per_sm_clk((double)threads * it_log));
+  const int it_logf = 1 << 12;
+  k_logf_tput<<<blocks, threads>>>(reinterpret_cast<float*>(d_out), d_cyc, it_logf);
+  CK(cudaDeviceSynchronize());
+  std::printf("float logf():                               %8.2f lane-ops/clk/SM\n",
+              per_sm_clk((double)threads * 4 * it_logf));
+  const int it_ph = 1 << 11;
+  k_philox_tput<<<blocks, threads>>>(reinterpret_cast<uint32_t*>(d_out), d_cyc, it_ph);
+  CK(cudaDeviceSynchronize());
+  const double ph = per_sm_clk((double)threads * it_ph);
+  std::printf("Philox4x32-10 (10 rounds):                  %8.3f calls/clk/SM (%.2e calls/s at the max clock)\n",
+              ph, ph * n_sm * khz * 1e3);
+
+  k_lds_lat<<<1, 32>>>(reinterpret_cast<int*>(d_out), d_cyc, 1 << 14);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&one, d_cyc, sizeof(long long), cudaMemcpyDeviceToHost));
+  std::printf("shared-memory load dependent latency:       %8.1f clk\n", (double)one / (1 << 14));
+  k_shfl_lat<<<1, 32>>>(reinterpret_cast<int*>(d_out), d_cyc, 1 << 14);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&one, d_cyc, sizeof(long long), cudaMemcpyDeviceToHost));
+  std::printf("warp shuffle (+1) dependent latency:        %8.1f clk\n", (double)one / (1 << 14));
+
+  // the sequential WL step: 64 walkers on 64 SMs, window of 216 bins (Ising 32x32, 16 windows)
+  const int W = 216, passes = 64, nb = 64;
+  const char* names[5] = {"dependency chain only", "+ band and conflict tests as a flag",
+                          "+ the tests as a branch out of the loop", "FP64 ln g, dependency chain only",
+                          "FP64 ln g, + the tests as a branch"};
+  for (int v = 0; v < 5; ++v) {
+    long long* o = reinterpret_cast<long long*>(d_out);
+    if (v == 0) k_chain<0><<<nb, 32>>>(W, passes, d_cyc, o);
+    if (v == 1) k_chain<1><<<nb, 32>>>(W, passes, d_cyc, o);
+    if (v == 2) k_chain<2><<<nb, 32>>>(W, passes, d_cyc, o);
+    if (v == 3) k_chain<0, double><<<nb, 32>>>(W, passes / 4, d_cyc, o);
+    if (v == 4) k_chain<2, double><<<nb, 32>>>(W, passes / 4, d_cyc, o);
+    CK(cudaDeviceSynchronize());
+    std::vector<long long> c(nb);
+    CK(cudaMemcpy(c.data(), d_cyc, sizeof(long long) * nb, cudaMemcpyDeviceToHost));
+    const int np = v >= 3 ? passes / 4 : passes;
+    std::printf("sequential WL step, %-38s %6.1f clk per trial\n", names[v], median(c) / ((double)np * kSteps));
+  }
+  CK(cudaFree(d_out));
+  CK(cudaFree(d_cyc));
+  return 0;
+}

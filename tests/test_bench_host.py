@@ -36,3 +36,19 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["cores"] == bench.host_cores() and line["cpu_baseline"]["kind"] == "oracle"
     assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_latency_bound_is_read_from_the_committed_summary():
+    assert 50.0 < bench.isolated_step_cycles() < 1000.0
+
+
+def test_rates_microbenchmark_builds():
+    import shutil
+
+    import pytest
+
+    if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
+        pytest.skip("no CUDA toolkit")
+    from paper_1305_5615_gb300 import ubench
+
+    assert os.path.exists(ubench.build())
