@@ -254,9 +254,12 @@ __device__ __forceinline__ uint32_t conflict_mask(const Problem& P, int x, int y
 
 template <int G>
 __device__ __forceinline__ uint32_t group_mask() {
-  if (G == 32) return 0xffffffffu;
-  const uint32_t lane = threadIdx.x & 31u;
-  return ((1u << G) - 1u) << (lane & ~(uint32_t)(G - 1));
+  if constexpr (G == 32) {
+    return 0xffffffffu;
+  } else {
+    const uint32_t lane = threadIdx.x & 31u;
+    return ((1u << G) - 1u) << (lane & ~(uint32_t)(G - 1));
+  }
 }
 
 template <int G, typename T>
@@ -453,7 +456,7 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
     uint32_t h_cur = s_H[bin * wpb + lw];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
     const uint32_t gm = group_mask<G>();
-    const int L = P.L, w = window_width(P, S, a);  // the window test; P.w is the layout stride
+    const int w = window_width(P, S, a);  // the window test; P.w is the layout stride
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
     StagedTrial* my_stage = s_stage + (size_t)lw * G;
 
@@ -582,9 +585,12 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
 // (shadow_end - shadow_start) / ln f, and the write-back adds it to H and
 // applies the same number of FP64 additions to ln g.  The shadow array
 // carries kGuardBins unused bins on each side so that speculative loads
-// need no clamping.
+// need no clamping: the current bin is always inside the window, one
+// trial moves at most 4 bins (Potts; 3 on the cube, 2 for Ising and the 2D
+// glass), and the furthest load, trial j+1's target after a move of trial
+// j, is two such offsets away.
 // ---------------------------------------------------------------------------
-constexpr int kGuardBins = 4;
+constexpr int kGuardBins = 8;
 
 // exact FP64 re-evaluation from visit counts reconstructed from the shadow
 __device__ __noinline__ bool exact_accept_fx(const DevState& S, const Problem& P, int W, int k, int bin,
@@ -752,11 +758,11 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   if (valid) {
     kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
     const int64_t lnf_fx = 1ll << (kFxBits - kexp);  // ln f >= 2^-39 (rewl_create checks ln f_final)
-    int64_t* fxp = s_fx + (size_t)kGuardBins * wpb + lw;  // fxp[b * wpb] = shadow of bin b, b in [-4, w+3]
+    int64_t* fxp = s_fx + (size_t)kGuardBins * wpb + lw;  // fxp[b * wpb] = shadow of bin b, b in [-8, w+7]
     int64_t fx_cur = fxp[bin * wpb];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
     const uint32_t gm = group_mask<G>();
-    const int L = P.L, w = window_width(P, S, a);  // the window test; P.w is the layout stride
+    const int w = window_width(P, S, a);  // the window test; P.w is the layout stride
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
     HotTrial* my_hot = s_hot + (size_t)lw * G;
     ColdTrial* my_cold = s_cold + (size_t)lw * G;
