@@ -324,7 +324,7 @@ def oracle_time_to_dos(wl, seeds, sweeps, limit_s):
 
 
 def run_reference(args, wl, world, rank):
-    """The reference arm: the plain CPU oracle on the machine's host cores, as P =
+    """The reference arm: the plain CPU oracle on the host's cores, as P =
     host_cores() independent solves (one thread each, seeds 0 .. P-1) that
     run their exchange blocks at the same time.  A step is one exchange block
     (100 sweeps) of every solve; the step's time is the slowest solve's."""
