@@ -216,6 +216,125 @@ __global__ void k_chain(int W, int passes, long long* cyc, long long* out) {
   out[blockIdx.x] = (long long)fx_cur + bin + bad;
 }
 
+// The same step with trial j+1's test made for both outcomes of trial j
+// before that outcome is known (the outcome then only selects between two
+// ready predicates): a candidate restructuring of the sweep kernel's fast
+// loop, measured here on its own.  Inputs and results as k_chain<0>.
+__global__ void k_chain_spec(int W, int passes, long long* cyc, long long* out) {
+  __shared__ int s_d[kSteps];
+  __shared__ long long s_thr[kSteps];
+  __shared__ long long s_fx[kMaxW + 8];
+  for (int i = threadIdx.x; i < kSteps; i += blockDim.x) {
+    const rewl::U4 r = rewl::philox10((uint32_t)i, blockIdx.x, 7u, 0u, 0x2468aceu, 0x13579bdu);
+    const uint32_t k = rewl::scale32(r.x, 16u);
+    s_d[i] = k < 6 ? 0 : k < 10 ? 1 : k < 14 ? -1 : k < 15 ? 2 : -2;
+    const float u = ((float)(r.y >> 8) + 0.5f) * 0x1p-24f;
+    s_thr[i] = fx_scale<long long>((double)logf(u));
+  }
+  for (int b = threadIdx.x; b < W + 8; b += blockDim.x) {
+    const double x = (double)(b - 4) / W;
+    s_fx[b] = fx_scale<long long>(200.0 * x * (1.0 - x) + 1.0);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  long long* fxp = s_fx + 4;
+  const long long lnf = 1ll << 30, guard = 1ll << 24;
+  int bin = W / 2, d = s_d[0];
+  long long fx_cur = fxp[bin], fxn = fxp[bin + d];
+  bool A = d == 0 || ((unsigned)(bin + d) < (unsigned)W && fxn < fx_cur - s_thr[0] - guard);
+  const long long t0 = clock64();
+  for (int p = 0; p < passes; ++p) {
+#pragma unroll 1
+    for (int j = 0; j < kSteps; ++j) {
+      const int j1 = (j + 1) & (kSteps - 1);
+      const int dn = s_d[j1];
+      const long long thr1 = s_thr[j1] + guard;
+      const int bn = bin + d;
+      const long long cs = fxp[bin + dn], cm = fxp[bn + dn];
+      const bool mv = A && d != 0;
+      if (mv) fxp[bin] = fx_cur;
+      const long long fwd = (dn == -d) ? fx_cur : cm;
+      const long long fcs = fx_cur + lnf, fcm = fxn + lnf;
+      const bool As = dn == 0 || ((unsigned)(bin + dn) < (unsigned)W && cs < fcs - thr1);
+      const bool Am = dn == 0 || ((unsigned)(bn + dn) < (unsigned)W && fwd < fcm - thr1);
+      A = mv ? Am : As;
+      fxn = mv ? fwd : cs;
+      fx_cur = mv ? fcm : fcs;
+      bin = mv ? bn : bin;
+      d = dn;
+    }
+  }
+  cyc[blockIdx.x] = clock64() - t0;
+  out[blockIdx.x] = fx_cur + bin;
+}
+
+// The same step with the candidate shadows loaded one trial further ahead:
+// in the iteration of trial j the shadows trial j+2 may target are loaded
+// for all four outcomes of trials j and j+1; the next iteration keeps the
+// two that trial j's outcome allows (with trial j's write-back forwarded).
+// A load then has a whole iteration to arrive instead of part of one.
+// Inputs and results as k_chain<0>.
+__global__ void k_chain_deep3(int W, int passes, long long* cyc, long long* out) {
+  __shared__ int s_d[kSteps];
+  __shared__ long long s_thr[kSteps];
+  __shared__ long long s_fx[kMaxW + 16];
+  for (int i = threadIdx.x; i < kSteps; i += blockDim.x) {
+    const rewl::U4 r = rewl::philox10((uint32_t)i, blockIdx.x, 7u, 0u, 0x2468aceu, 0x13579bdu);
+    const uint32_t k = rewl::scale32(r.x, 16u);
+    s_d[i] = k < 6 ? 0 : k < 10 ? 1 : k < 14 ? -1 : k < 15 ? 2 : -2;
+    const float u = ((float)(r.y >> 8) + 0.5f) * 0x1p-24f;
+    s_thr[i] = fx_scale<long long>((double)logf(u));
+  }
+  for (int b = threadIdx.x; b < W + 16; b += blockDim.x) {  // the same shadow as k_chain, 8 guard bins
+    const double x = (double)(b - 8) / W;
+    s_fx[b] = fx_scale<long long>(200.0 * x * (1.0 - x) + 1.0);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  long long* fxp = s_fx + 8;  // bins -8 .. W+7; loads reach B + 3 offsets of at most 2
+  const long long lnf = 1ll << 30, guard = 1ll << 24;
+  int B = W / 2;
+  long long X = fxp[B], Y = fxp[B + s_d[0]];
+  long long Rss = fxp[B + s_d[1]], Rsm = fxp[B + s_d[0] + s_d[1]], Rms = Rss, Rmm = Rsm;
+  bool mvp = false;
+  int Bp = B;
+  long long Xp = X;
+  const long long t0 = clock64();
+  for (int p = 0; p < passes; ++p) {
+#pragma unroll 1
+    for (int j = 0; j < kSteps; ++j) {
+      const int dj = s_d[j], d1 = s_d[(j + 1) & (kSteps - 1)], d2 = s_d[(j + 2) & (kSteps - 1)];
+      const long long thr = s_thr[j];
+      // loads for trial j+2 (memory holds every write-back up to trial j-1)
+      const long long nss = fxp[B + d2], nsm = fxp[B + d1 + d2], nms = fxp[B + dj + d2], nmm = fxp[B + dj + d1 + d2];
+      // trial j+1's candidates from the loads of the last iteration
+      const int Ts = B + d1, Tm = B + dj + d1;
+      long long Cs = mvp ? Rms : Rss, Cm = mvp ? Rmm : Rsm;
+      if (mvp && Ts == Bp) Cs = Xp;
+      if (mvp && Tm == Bp) Cm = Xp;
+      // trial j
+      const int bn = B + dj;
+      const bool acc = dj == 0 || ((unsigned)bn < (unsigned)W && Y < X - thr - guard);
+      const bool mv = acc && dj != 0;
+      if (mv) fxp[B] = X;
+      const long long Yn = mv ? (d1 == -dj ? X : Cm) : Cs;
+      const long long Xn = (mv ? Y : X) + lnf;
+      mvp = mv;
+      Bp = B;
+      Xp = X;
+      Rss = nss;
+      Rsm = nsm;
+      Rms = nms;
+      Rmm = nmm;
+      B = mv ? bn : B;
+      X = Xn;
+      Y = Yn;
+    }
+  }
+  cyc[blockIdx.x] = clock64() - t0;
+  out[blockIdx.x] = X + B;
+}
+
 double median(std::vector<long long> v) {
   std::sort(v.begin(), v.end());
   return (double)v[v.size() / 2];
@@ -280,21 +399,31 @@ int main() {
 
   // the sequential WL step: 64 walkers on 64 SMs, window of 216 bins (Ising 32x32, 16 windows)
   const int W = 216, passes = 64, nb = 64;
-  const char* names[5] = {"dependency chain only", "+ band and conflict tests as a flag",
+  const char* names[7] = {"dependency chain only", "+ band and conflict tests as a flag",
                           "+ the tests as a branch out of the loop", "FP64 ln g, dependency chain only",
-                          "FP64 ln g, + the tests as a branch"};
-  for (int v = 0; v < 5; ++v) {
+                          "FP64 ln g, + the tests as a branch", "next test made for both outcomes",
+                          "candidate loads a trial further ahead"};
+  std::vector<long long> ref;
+  for (int v = 0; v < 7; ++v) {
     long long* o = reinterpret_cast<long long*>(d_out);
     if (v == 0) k_chain<0><<<nb, 32>>>(W, passes, d_cyc, o);
     if (v == 1) k_chain<1><<<nb, 32>>>(W, passes, d_cyc, o);
     if (v == 2) k_chain<2><<<nb, 32>>>(W, passes, d_cyc, o);
     if (v == 3) k_chain<0, double><<<nb, 32>>>(W, passes / 4, d_cyc, o);
     if (v == 4) k_chain<2, double><<<nb, 32>>>(W, passes / 4, d_cyc, o);
+    if (v == 5) k_chain_spec<<<nb, 32>>>(W, passes, d_cyc, o);
+    if (v == 6) k_chain_deep3<<<nb, 32>>>(W, passes, d_cyc, o);
     CK(cudaDeviceSynchronize());
     std::vector<long long> c(nb);
     CK(cudaMemcpy(c.data(), d_cyc, sizeof(long long) * nb, cudaMemcpyDeviceToHost));
-    const int np = v >= 3 ? passes / 4 : passes;
+    const int np = v == 3 || v == 4 ? passes / 4 : passes;
     std::printf("sequential WL step, %-38s %6.1f clk per trial\n", names[v], median(c) / ((double)np * kSteps));
+    if (v == 0 || v >= 5) {  // these must walk the same chain
+      std::vector<long long> r(nb);
+      CK(cudaMemcpy(r.data(), o, sizeof(long long) * nb, cudaMemcpyDeviceToHost));
+      if (v == 0) ref = r;
+      else std::printf("  (same final states as the chain-only form: %s)\n", r == ref ? "yes" : "NO");
+    }
   }
   CK(cudaFree(d_out));
   CK(cudaFree(d_cyc));
