@@ -372,16 +372,6 @@ __device__ __forceinline__ TrialEval<MODEL> eval_trial(const Problem& P, const u
   return t;
 }
 
-template <int MODEL>
-__device__ __forceinline__ void apply_move(uint32_t* s_lat, uint32_t widx, uint32_t wmask) {
-  if constexpr (MODEL == kPotts) {
-    const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
-    s_lat[widx] = (s_lat[widx] & ~(15u << sh)) | (nv << sh);
-  } else {
-    s_lat[widx] ^= wmask;
-  }
-}
-
 // One staged trial: what the parallel phase hands to the sequential phase.
 struct StagedTrial {
   uint32_t pk;     // dbin + 8 | pv << 8 | x << 16 | y << 24
@@ -580,6 +570,9 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
 // bins trial j+1 can target (from the current bin, and from trial j's new
 // bin); once trial j's outcome is known one of the two is selected, with the
 // register value forwarded when the target is the bin trial j just left.
+// The sequential step does not write the configuration: after each group the
+// lanes write their own accepted moves (one XOR each), and a trial that meets
+// an earlier accepted one first writes the moves its neighbourhood depends on.
 // H is not kept during the launch: the shadow of a bin grows by exactly
 // ln f (in 2^-40 units) per visit, so the visit count of every bin is
 // (shadow_end - shadow_start) / ln f, and the write-back adds it to H and
@@ -608,18 +601,6 @@ __device__ __noinline__ bool exact_accept_fx(const DevState& S, const Problem& P
   const double lu = log(u);
   if (fabs(__dsub_rn(lu, delta)) < 1e-12) ++n_tie;
   return lu < delta;
-}
-
-template <int MODEL>
-__device__ __forceinline__ void apply_move_if(uint32_t* s_lat, uint32_t widx, uint32_t wmask, bool acc) {
-  if constexpr (MODEL == kPotts) {
-    if (acc) {
-      const uint32_t sh = wmask & 0xffu, nv = wmask >> 8;
-      s_lat[widx] = (s_lat[widx] & ~(15u << sh)) | (nv << sh);
-    }
-  } else {
-    atomicXor(&s_lat[widx], acc ? wmask : 0u);
-  }
 }
 
 // ---------------------------------------------------------------------------
