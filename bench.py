@@ -254,6 +254,14 @@ def host_cores():
     return os.cpu_count() or 1
 
 
+def _run_threads(fn, n):
+    th = [threading.Thread(target=fn, args=(k,)) for k in range(n)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+
+
 def oracle_rate_all_cores(wl, seed, seconds):
     """P = host_cores() independent oracle solves (seeds seed .. seed+P-1),
     one thread each, run at the same time: aggregate attempts/s.  The
@@ -264,17 +272,19 @@ def oracle_rate_all_cores(wl, seed, seconds):
     (rate, P, seconds, walkers sampled per solve)."""
     P = host_cores()
     h, m = _oracle_sample_shape(wl, seconds)
-    bar = threading.Barrier(P)
-    res = [None] * P
+    bar = threading.Barrier(P, timeout=600.0)
+    res, err = [None] * P, []
 
     def work(k):
-        res[k] = _oracle_blocks(wl, h, m, seed + k, seconds, bar)
+        try:
+            res[k] = _oracle_blocks(wl, h, m, seed + k, seconds, bar)
+        except BaseException as e:  # a failed solve breaks the barrier for the others
+            bar.abort()
+            err.append(e)
 
-    th = [threading.Thread(target=work, args=(k,)) for k in range(P)]
-    for t in th:
-        t.start()
-    for t in th:
-        t.join()
+    _run_threads(work, P)
+    if err:
+        raise RuntimeError("oracle timing failed: %r" % (err[0],))
     att = sum(r[0] for r in res)
     el = max(r[1] for r in res)
     return att / el, P, el, h * m
@@ -338,13 +348,19 @@ def run_reference(args, wl, world, rank):
     solves = [OracleREWL(wl["model"], wl["L"], h, OVERLAP, m, FLATNESS, wl["lnf_final"], k, q=wl["q"],
                          sweeps_per_exchange=SPE, sweeps_per_flat_check=SPF) for k in range(P)]
 
+    err = []
+
+    def block(k):
+        try:
+            solves[k].run_blocks(1)
+        except BaseException as e:
+            err.append(e)
+
     def one_step():
-        th = [threading.Thread(target=O.run_blocks, args=(1,)) for O in solves]
         t0 = time.perf_counter()
-        for t in th:
-            t.start()
-        for t in th:
-            t.join()
+        _run_threads(block, P)
+        if err:
+            raise RuntimeError("oracle block failed: %r" % (err[0],))
         return time.perf_counter() - t0
 
     for _ in range(args.warmup):

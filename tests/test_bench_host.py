@@ -52,3 +52,21 @@ def test_rates_microbenchmark_builds():
     from paper_1305_5615_gb300 import ubench
 
     assert os.path.exists(ubench.build())
+
+
+def test_all_cores_timing_fails_loudly_when_one_solve_fails(monkeypatch):
+    """One failing oracle solve must end the all-cores sample with an error,
+    not leave the others waiting at the start barrier."""
+    import pytest
+
+    real = bench._oracle_blocks
+
+    def flaky(wl, h, m, seed, seconds, barrier=None):
+        if seed == 1:
+            raise ValueError("planted failure")
+        return real(wl, h, m, seed, seconds, barrier)
+
+    monkeypatch.setattr(bench, "_oracle_blocks", flaky)
+    monkeypatch.setattr(bench, "host_cores", lambda: 3)
+    with pytest.raises(RuntimeError, match="planted failure"):
+        bench.oracle_rate_all_cores(bench.WORKLOADS["ising-L8-h4-m2"], 0, 0.5)
