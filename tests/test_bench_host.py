@@ -70,3 +70,24 @@ def test_all_cores_timing_fails_loudly_when_one_solve_fails(monkeypatch):
     monkeypatch.setattr(bench, "host_cores", lambda: 3)
     with pytest.raises(RuntimeError, match="planted failure"):
         bench.oracle_rate_all_cores(bench.WORKLOADS["ising-L8-h4-m2"], 0, 0.5)
+
+
+def test_fifo_latencies_follow_the_queue_by_hand():
+    """One server, first come first served: arrivals 0, 1, 5 with services 3, 1, 2
+    finish at 3, 4, 7, so the latencies are 3, 3, 2."""
+    assert bench._fifo_latencies([0.0, 1.0, 5.0], [3.0, 1.0, 2.0]) == [3.0, 3.0, 2.0]
+    assert bench._fifo_latencies([], []) == []
+
+
+def test_served_stream_mix():
+    """The served stream: one third of each model, each model's own sizes,
+    q = 10 for Potts, request seed = index."""
+    reqs = bench.served_requests(3000, 0)
+    sizes = {m: set(s) for m, s, _ in bench.SERVED_MIX}
+    counts = {m: 0 for m in sizes}
+    for i, r in enumerate(reqs):
+        assert r["seed"] == i and r["L"] in sizes[r["model"]]
+        assert r["q"] == (10 if r["model"] == "potts" else 2)
+        counts[r["model"]] += 1
+    assert all(abs(c / 3000 - 1 / 3) < 0.04 for c in counts.values())
+    assert bench.served_requests(50, 7) == bench.served_requests(50, 7)
