@@ -335,6 +335,80 @@ __global__ void k_chain_deep3(int W, int passes, long long* cyc, long long* out)
   out[blockIdx.x] = X + B;
 }
 
+// The step with the band and conflict tests of two trials folded into one
+// branch: trial j+1 is evaluated from trial j's outcome as if trial j needed
+// no slow path, its write-back is predicated on neither needing it, and the
+// loop leaves (for the slow path; never taken here but on the rare band case)
+// once per pair.  Inputs as k_chain<1>.
+__global__ void k_chain_pair(int W, int passes, long long* cyc, long long* out) {
+  __shared__ int s_d[kSteps];
+  __shared__ long long s_thr[kSteps];
+  __shared__ unsigned s_mask[kSteps];
+  __shared__ long long s_fx[kMaxW + 8];
+  for (int i = threadIdx.x; i < kSteps; i += blockDim.x) {
+    const rewl::U4 r = rewl::philox10((uint32_t)i, blockIdx.x, 7u, 0u, 0x2468aceu, 0x13579bdu);
+    const uint32_t k = rewl::scale32(r.x, 16u);
+    s_d[i] = k < 6 ? 0 : k < 10 ? 1 : k < 14 ? -1 : k < 15 ? 2 : -2;
+    const float u = ((float)(r.y >> 8) + 0.5f) * 0x1p-24f;
+    s_thr[i] = fx_scale<long long>((double)logf(u));
+    s_mask[i] = 0u;
+  }
+  for (int b = threadIdx.x; b < W + 8; b += blockDim.x) {
+    const double x = (double)(b - 4) / W;
+    s_fx[b] = fx_scale<long long>(200.0 * x * (1.0 - x) + 1.0);
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  long long* fxp = s_fx + 4;
+  const long long lnf = 1ll << 30, guard = 1ll << 24;
+  int bin = W / 2, d = s_d[0];
+  long long fx_cur = fxp[bin], fxn = fxp[bin + d];
+  unsigned accm = 0, bad = 0;
+  const long long t0 = clock64();
+  for (int p = 0; p < passes; ++p) {
+#pragma unroll 1
+    for (int j = 0; j < kSteps; j += 2) {
+      const int d1 = s_d[j + 1], d2 = s_d[(j + 2) & (kSteps - 1)];
+      const long long thr0 = s_thr[j], thr1 = s_thr[j + 1];
+      const unsigned m0 = s_mask[j], m1 = s_mask[j + 1];
+      // trial j
+      const int bn = bin + d;
+      const long long cs = fxp[bin + d1], cm = fxp[bn + d1];
+      const bool in0 = (unsigned)bn < (unsigned)W;
+      const long long la0 = fx_cur - thr0 - guard, lr0 = fx_cur - thr0 + guard;
+      const bool acc0 = d == 0 || (in0 && fxn < la0);
+      const bool hit0 = (d != 0 && in0 && fxn >= la0 && fxn <= lr0) || (accm & m0) != 0u;
+      const bool mv0 = acc0 && d != 0;
+      if (mv0 && !hit0) fxp[bin] = fx_cur;
+      const long long fwd0 = (d1 == -d) ? fx_cur : cm;
+      const long long x1 = (mv0 ? fxn : fx_cur) + lnf, y1 = mv0 ? fwd0 : cs;
+      const int b1 = mv0 ? bn : bin;
+      const unsigned accm1 = (accm << 1) | (unsigned)acc0;
+      // trial j+1, as if trial j needed no slow path
+      const int bn1 = b1 + d1;
+      const long long cs1 = fxp[b1 + d2], cm1 = fxp[bn1 + d2];
+      const bool in1 = (unsigned)bn1 < (unsigned)W;
+      const long long la1 = x1 - thr1 - guard, lr1 = x1 - thr1 + guard;
+      const bool acc1 = d1 == 0 || (in1 && y1 < la1);
+      const bool hit1 = (d1 != 0 && in1 && y1 >= la1 && y1 <= lr1) || (accm1 & m1) != 0u;
+      const bool mv1 = acc1 && d1 != 0;
+      if (mv1 && !hit0 && !hit1) fxp[b1] = x1;
+      if (hit0 || hit1) {  // the slow path would take over here
+        bad += 1u + (unsigned)j;
+        break;
+      }
+      const long long fwd1 = (d2 == -d1) ? x1 : cm1;
+      fx_cur = (mv1 ? y1 : x1) + lnf;
+      fxn = mv1 ? fwd1 : cs1;
+      bin = mv1 ? bn1 : b1;
+      accm = (accm1 << 1) | (unsigned)acc1;
+      d = d2;
+    }
+  }
+  cyc[blockIdx.x] = clock64() - t0;
+  out[blockIdx.x] = fx_cur + bin + bad;
+}
+
 double median(std::vector<long long> v) {
   std::sort(v.begin(), v.end());
   return (double)v[v.size() / 2];
@@ -399,12 +473,12 @@ int main() {
 
   // the sequential WL step: 64 walkers on 64 SMs, window of 216 bins (Ising 32x32, 16 windows)
   const int W = 216, passes = 64, nb = 64;
-  const char* names[7] = {"dependency chain only", "+ band and conflict tests as a flag",
+  const char* names[8] = {"dependency chain only", "+ band and conflict tests as a flag",
                           "+ the tests as a branch out of the loop", "FP64 ln g, dependency chain only",
                           "FP64 ln g, + the tests as a branch", "next test made for both outcomes",
-                          "candidate loads a trial further ahead"};
+                          "candidate loads a trial further ahead", "+ the tests as one branch per pair"};
   std::vector<long long> ref;
-  for (int v = 0; v < 7; ++v) {
+  for (int v = 0; v < 8; ++v) {
     long long* o = reinterpret_cast<long long*>(d_out);
     if (v == 0) k_chain<0><<<nb, 32>>>(W, passes, d_cyc, o);
     if (v == 1) k_chain<1><<<nb, 32>>>(W, passes, d_cyc, o);
@@ -413,12 +487,13 @@ int main() {
     if (v == 4) k_chain<2, double><<<nb, 32>>>(W, passes / 4, d_cyc, o);
     if (v == 5) k_chain_spec<<<nb, 32>>>(W, passes, d_cyc, o);
     if (v == 6) k_chain_deep3<<<nb, 32>>>(W, passes, d_cyc, o);
+    if (v == 7) k_chain_pair<<<nb, 32>>>(W, passes, d_cyc, o);
     CK(cudaDeviceSynchronize());
     std::vector<long long> c(nb);
     CK(cudaMemcpy(c.data(), d_cyc, sizeof(long long) * nb, cudaMemcpyDeviceToHost));
     const int np = v == 3 || v == 4 ? passes / 4 : passes;
     std::printf("sequential WL step, %-38s %6.1f clk per trial\n", names[v], median(c) / ((double)np * kSteps));
-    if (v == 0 || v >= 5) {  // these must walk the same chain
+    if (v == 0 || v == 5 || v == 6) {  // these must walk the same chain
       std::vector<long long> r(nb);
       CK(cudaMemcpy(r.data(), o, sizeof(long long) * nb, cudaMemcpyDeviceToHost));
       if (v == 0) ref = r;
