@@ -484,6 +484,8 @@ rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* q, uint
       q->lattice.periodic != 1 || L < 2 || L > (dim == 3 ? 64 : 256) || q->windows < 1 ||
       q->walkers_per_window < 1 || q->walkers_per_window > 4096 || !(q->overlap > 0.0 && q->overlap < 1.0))
     return sfail(REWL_EINVAL, "invalid request");
+  if (!(q->flatness > 0.0 && q->flatness <= 1.0) || !(q->lnf_final >= 1e-12))
+    return sfail(REWL_EINVAL, "flatness must be in (0, 1] and lnf_final >= 1e-12");
   const bool pmj = q->model.kind == REWL_EA_PM_J || q->model.kind == REWL_EA_PM_J_3D;
   if (!pmj && q->couplings) return sfail(REWL_EINVAL, "couplings are only taken by +-J");
   std::lock_guard<std::mutex> lock(s->mu);

@@ -92,6 +92,10 @@ def test_bad_requests():
         S.submit("ising", 8, 4, 1.5, 2, 0.8, 1e-4, 1)
     with pytest.raises(rewl.RewlError):
         S.submit("ising", 300, 4, 0.75, 2, 0.8, 1e-4, 1)
+    for flatness, lnf_final in ((0.0, 1e-4), (1.5, 1e-4), (0.8, 0.0), (0.8, 1e-13)):  # malformed: refused at once
+        with pytest.raises(rewl.RewlError) as e:
+            S.submit("ising", 8, 4, 0.75, 2, flatness, lnf_final, 1)
+        assert e.value.status == 1
     # fails at admission (windows narrower than 3 bins), reported as a failed request
     rid = S.submit("ising", 8, 200, 0.75, 1, 0.8, 1e-4, 1)
     S.run(1)
