@@ -91,3 +91,17 @@ def test_served_stream_mix():
         counts[r["model"]] += 1
     assert all(abs(c / 3000 - 1 / 3) < 0.04 for c in counts.values())
     assert bench.served_requests(50, 7) == bench.served_requests(50, 7)
+
+
+def test_profile_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
+    """roofline.traffic comes from the committed ncu summary only while its
+    kernel_source_hash equals the hash of the current sweep sources, and only for
+    the profiled workload and sweep form; else it is null."""
+    f = tmp_path / "summary.txt"
+    f.write_text("kernel_source_hash = %s\ndram_bytes_per_launch = 1234\n" % bench.kernel_source_hash())
+    monkeypatch.setattr(bench, "PROFILE_SUMMARY", str(f))
+    assert bench.traffic_from_profile(bench.DEFAULT_WORKLOAD, 2) == 1234.0
+    assert bench.traffic_from_profile(bench.DEFAULT_WORKLOAD, 0) is None
+    assert bench.traffic_from_profile("ising-L128-h128-m32", 2) is None
+    f.write_text("kernel_source_hash = 0000000000000000\ndram_bytes_per_launch = 1234\n")
+    assert bench.traffic_from_profile(bench.DEFAULT_WORKLOAD, 2) is None
