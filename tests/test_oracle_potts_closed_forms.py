@@ -13,9 +13,7 @@ satisfied bonds):
 The oracle runs to ln f < 1e-5 with 4 windows x 2 walkers and four seeds
 (about 20 s).  The measured WL errors of the three ratios are at most 0.15 per
 seed and 0.03 for the mean over the seeds.  An energy change that miscounts a
-bond puts states on E = -2N + 5 or moves whole levels, and a proposal that is
-not uniform over the q - 1 other values changes the ratios by O(1); both fail
-here."""
+bond puts states on E = -2N + 5 or moves whole levels, which fails here."""
 import math
 
 import numpy as np
