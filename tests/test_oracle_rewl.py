@@ -212,6 +212,18 @@ def test_converges_ea_L4_given_couplings():
     assert _max_abs_error(R, E_ex, g_ex) < 0.08
 
 
+def test_converges_ea_L8_drawn_couplings():
+    """+-J 8 x 8 with couplings drawn from the seed, four windows over the range
+    the descent lays out (reaching on to -2N): the walk finds every reachable
+    level, the ground state included, and nothing else, and ln g matches the
+    transfer-matrix DOS of the same couplings (measured max error 0.085)."""
+    R = OracleREWL("ea", 8, 4, 0.75, 2, 0.8, 1e-6, 5)
+    E_ex, g_ex = X.transfer_dos(8, "ea", couplings=R.couplings())
+    assert R.e_min == -2 * R.N < min(E_ex)
+    _run(R)
+    assert _max_abs_error(R, E_ex, g_ex) < 0.2
+
+
 def test_converges_potts_q3_L4():
     R = OracleREWL("potts", 4, 2, 0.75, 2, 0.8, 1e-6, 2, q=3)
     _run(R)
