@@ -66,6 +66,10 @@ def lib():
         L.orc_destroy.argtypes = [P]
         L.orc_run_blocks.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]
         L.orc_run_blocks.restype = ctypes.c_int
+        L.orc_active_windows.argtypes = [P]
+        L.orc_active_windows.restype = ctypes.c_int
+        L.orc_block_sweeps.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        L.orc_block_finish.argtypes = [P]
         L.orc_info.argtypes = [P, P]
         L.orc_get_windows.argtypes = [P, P, P, P, P]
         L.orc_get_phase.argtypes = [P, P]
@@ -140,12 +144,30 @@ class OracleREWL:
     def __del__(self):
         self.close()
 
-    def run_blocks(self, n_blocks):
-        done = ctypes.c_int(0)
-        st = self._lib.orc_run_blocks(self._h, n_blocks, ctypes.byref(done))
-        if st != 0:
-            raise RuntimeError("orc_run_blocks failed with status %d" % st)
-        return bool(done.value)
+    def run_blocks(self, n_blocks, threads=1):
+        """Runs n_blocks blocks (sweeps, exchange round, flatness check when
+        due).  threads > 1 sweeps disjoint walker ranges of each block on that
+        many host threads (orc_block_sweeps; the walkers of a block are
+        independent, so the trials and results are the same), then finishes
+        the block on this thread.  Returns True when every window is done."""
+        if threads <= 1:
+            done = ctypes.c_int(0)
+            st = self._lib.orc_run_blocks(self._h, n_blocks, ctypes.byref(done))
+            if st != 0:
+                raise RuntimeError("orc_run_blocks failed with status %d" % st)
+            return bool(done.value)
+        import concurrent.futures
+
+        n = self.h * self.m
+        cuts = [n * i // threads for i in range(threads + 1)]
+        ranges = [(cuts[i], cuts[i + 1]) for i in range(threads) if cuts[i + 1] > cuts[i]]
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(ranges)) as ex:
+            for _ in range(n_blocks):
+                if self._lib.orc_active_windows(self._h) == 0:
+                    break
+                list(ex.map(lambda r: self._lib.orc_block_sweeps(self._h, r[0], r[1]), ranges))
+                self._lib.orc_block_finish(self._h)
+        return self._lib.orc_active_windows(self._h) == 0
 
     def info(self):
         a = np.zeros(16, dtype=np.int64)

@@ -637,33 +637,49 @@ static void one_over_t_step(orc_rewl* R, int a) {
 /* check.  One sweep = N trial moves per walker.  Attempt t of a walker is  */
 /* t = sweep_clock * N + i; all walkers of active windows move in lockstep. */
 /* ------------------------------------------------------------------------ */
-int orc_run_blocks(orc_rewl* R, int64_t n_blocks, int* all_done) {
-  int h = R->h, m = R->m, N = R->N;
-  for (int64_t blk = 0; blk < n_blocks; ++blk) {
-    int active = 0;
-    for (int a = 0; a < h; ++a) active += !R->done[a];
-    if (!active) break;
-    uint64_t t0 = R->sweep_clock * (uint64_t)N;
-    uint64_t n_att = (uint64_t)R->params.sweeps_per_exchange * (uint64_t)N;
+/* Number of windows not done yet. */
+int orc_active_windows(const orc_rewl* R) {
+  int active = 0;
+  for (int a = 0; a < R->h; ++a) active += !R->done[a];
+  return active;
+}
+
+/* The WL sweeps of the current block for walkers W0 .. W1-1 of the windows
+ * not done.  A walker's sweeps read and write only its own configuration,
+ * energy, ln g, H and counters, so disjoint walker ranges of one block may
+ * run on different host threads (same trials, same results). */
+void orc_block_sweeps(orc_rewl* R, int W0, int W1) {
+  uint64_t t0 = R->sweep_clock * (uint64_t)R->N;
+  uint64_t n_att = (uint64_t)R->params.sweeps_per_exchange * (uint64_t)R->N;
+  for (int W = W0; W < W1 && W < R->h * R->m; ++W) {
+    if (R->done[W / R->m]) continue;
+    for (uint64_t i = 0; i < n_att; ++i) wl_attempt(R, W, t0 + i);
+  }
+}
+
+/* The rest of the block, after every walker's sweeps: the clock, one
+ * exchange round and, when due, the flatness check of every window. */
+void orc_block_finish(orc_rewl* R) {
+  int h = R->h;
+  R->sweep_clock += (uint64_t)R->params.sweeps_per_exchange;
+  for (int a = (int)(R->xround % 2u); a + 1 < h; a += 2)
+    if (!R->done[a] && !R->done[a + 1]) exchange_pair(R, a, R->xround);
+  R->xround += 1u;
+  if (R->sweep_clock % (uint64_t)R->params.sweeps_per_flat_check == 0)
     for (int a = 0; a < h; ++a) {
       if (R->done[a]) continue;
-      for (int k = 0; k < m; ++k)
-        for (uint64_t i = 0; i < n_att; ++i) wl_attempt(R, a * m + k, t0 + i);
+      if (R->params.wl_rule == 1) one_over_t_step(R, a);
+      else flatness_and_merge(R, a);
     }
-    R->sweep_clock += (uint64_t)R->params.sweeps_per_exchange;
-    for (int a = (int)(R->xround % 2u); a + 1 < h; a += 2)
-      if (!R->done[a] && !R->done[a + 1]) exchange_pair(R, a, R->xround);
-    R->xround += 1u;
-    if (R->sweep_clock % (uint64_t)R->params.sweeps_per_flat_check == 0)
-      for (int a = 0; a < h; ++a) {
-        if (R->done[a]) continue;
-        if (R->params.wl_rule == 1) one_over_t_step(R, a);
-        else flatness_and_merge(R, a);
-      }
+}
+
+int orc_run_blocks(orc_rewl* R, int64_t n_blocks, int* all_done) {
+  for (int64_t blk = 0; blk < n_blocks; ++blk) {
+    if (!orc_active_windows(R)) break;
+    orc_block_sweeps(R, 0, R->h * R->m);
+    orc_block_finish(R);
   }
-  int d = 1;
-  for (int a = 0; a < h; ++a) d &= R->done[a];
-  if (all_done) *all_done = d;
+  if (all_done) *all_done = orc_active_windows(R) == 0;
   return ORC_OK;
 }
 

@@ -59,6 +59,9 @@ int orc_create(orc_rewl** out, int model, int q, int L, const int8_t* couplings,
                double flatness, double lnf_final, uint64_t seed, const orc_params* params);
 void orc_destroy(orc_rewl* R);
 int orc_run_blocks(orc_rewl* R, int64_t n_blocks, int* all_done);
+int orc_active_windows(const orc_rewl* R);
+void orc_block_sweeps(orc_rewl* R, int W0, int W1);
+void orc_block_finish(orc_rewl* R);
 int orc_energy(const orc_rewl* R, const uint8_t* s);
 int orc_walker_is_flat(const orc_rewl* R, int W);
 void orc_info(const orc_rewl* R, int64_t* info);

@@ -92,6 +92,46 @@ def test_merge_shares_ln_g_and_resets_H():
     assert win["lnf"][a] == 0.5 ** win["iteration"][a]
 
 
+def test_merge_value_is_the_walker_order_mean():
+    """The merged ln g is the mean of the window's m estimators (merge
+    paragraph: the estimators are averaged), summed in walker order and
+    divided by m, bit for bit.  ln g is frozen (ln f = 0 in every window) at
+    four distinct hand-made tables per window and H at a large flat level, so
+    the first check finds every walker flat and merges: copying one walker's
+    table, dropping a walker, averaging another window's walkers or summing in
+    another order all change the bits."""
+    m = 4
+    R = OracleREWL("ising", 4, 2, 0.75, m, 0.8, 1e-4, 17, sweeps_per_exchange=10, sweeps_per_flat_check=100)
+    rng = np.random.default_rng(5)
+    win = R.windows()
+    tables = {}
+    for a in range(R.h):
+        R.set_window_lnf(a, 0.0)
+        for k in range(m):
+            W = a * m + k
+            t = np.zeros(R.w)
+            # distinct per walker, positive on the window's bins (all count as visited), not dyadic
+            t[:win["width"][a]] = rng.uniform(1.0, 50.0, size=win["width"][a]) * (1.0 + 0.37 * k) + 0.1 * a
+            tables[W] = t
+            R.set_walker_lng(W, t)
+            R.set_walker_H(W, np.full(R.w, 10 ** 6, np.uint32))
+    R.run_blocks(10)  # 100 sweeps: one flatness check
+    win = R.windows()
+    assert (win["iteration"] == 1).all()
+    st = R.walkers()
+    for a in range(R.h):
+        s = tables[a * m].copy()
+        for k in range(1, m):
+            s = s + tables[a * m + k]
+        mean = s / float(m)
+        for k in range(m):
+            assert np.array_equal(st["lng"][a * m + k].view(np.uint64), mean.view(np.uint64)), (a, k)
+        # a plausible mistake changes the value: one walker's table, or a sum without walker m-1
+        assert not np.array_equal(mean, tables[a * m])
+        assert not np.array_equal(mean, (s - tables[a * m + m - 1]) / float(m - 1))
+    assert not st["H"].any()
+
+
 def test_phase_schedule_counts_exchanges():
     R = OracleREWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 2, sweeps_per_exchange=50, sweeps_per_flat_check=1000)
     R.run_blocks(6)
@@ -125,6 +165,39 @@ def test_flatness_rule():
     assert R.walker_is_flat(0)
     R.set_walker_lng(0, np.zeros(R.w))
     assert not R.walker_is_flat(0)   # nothing visited is not flat
+
+
+def test_flatness_on_the_exact_four_fifths_boundary():
+    """Flatness 0.8 is tested in FP64 as min H * n >= 0.8 * sum H.  On the
+    exact rational boundary 5 min H n = 4 sum H it agrees with the exact test
+    (flat), and one count below the boundary it is not flat."""
+    R = OracleREWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, sweeps_per_flat_check=100000)
+    lng = np.zeros(R.w)
+    lng[:10] = 1.0
+    R.set_walker_lng(0, lng)
+    # n = 10 visited bins, min H = 80, sum H = 5 * 80 * 10 / 4 = 1000
+    H = np.zeros(R.w, np.uint32)
+    H[:10] = [80, 80, 80, 80, 80, 120, 120, 120, 120, 120]
+    assert 5 * 80 * 10 == 4 * int(H.sum())
+    R.set_walker_H(0, H)
+    assert R.walker_is_flat(0)
+    H[9] += 1          # sum 1001: 5 * 80 * 10 < 4 * 1001
+    R.set_walker_H(0, H)
+    assert not R.walker_is_flat(0)
+    # larger counts, still on the boundary: min H = 4k, n = 8, sum H = 40k
+    lng[:] = 0.0
+    lng[:8] = 2.0
+    R.set_walker_lng(0, lng)
+    for kk in (1, 7, 12345, 999983):
+        H = np.zeros(R.w, np.uint32)
+        H[:8] = 4 * kk
+        H[0] += 8 * kk   # sum = 32k + 8k = 40k = 5 * (4k) * 8 / 4
+        R.set_walker_H(0, H)
+        assert 5 * int(H[:8].min()) * 8 == 4 * int(H.sum())
+        assert R.walker_is_flat(0), kk
+        H[1] += 1
+        R.set_walker_H(0, H)
+        assert not R.walker_is_flat(0), kk
 
 
 # ----------------------------------------------------- Eq. (1): detailed balance
