@@ -481,7 +481,7 @@ def run_gb300(args, wl, world, rank, local):
             roof["latency"] = {"unit": "clk/trial per walker", "kernel": cyc, "isolated_step": iso,
                                "frac": iso / cyc, "sm_mhz": f_run,
                                "basis": "the sequential WL step alone (dependency chain only), measured by "
-                                        "paper_1305_5615_gb300/ubench on the GB300"}
+                                        "ubench/rates.cu on the GB300"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -113,6 +113,11 @@ typedef struct {
                                     read at rewl_create.  Must cover bins 0 .. n_bins-1 with widths >= 3,
                                     strictly increasing starts and ends, neighbours sharing >= 1 bin */
   const int32_t* window_widths;  /* `windows` widths in bins, with window_starts (both or neither) */
+  int64_t wait_cycles;           /* bound of the ring form's hand-off waits between a walker's warp and
+                                    its producer warp, in SM clock cycles from the start of a sweep
+                                    launch; 0 = 2^34 (about 8 s at 2 GHz, while a launch takes
+                                    milliseconds).  When a wait runs out both warps stop early and
+                                    rewl_step returns REWL_ETIMEOUT at its next flatness check */
 } rewl_params;
 
 /*
@@ -471,34 +476,47 @@ void rewl_server_destroy(rewl_server_handle s);
  * exchange, no flatness check.  All pointers are DEVICE pointers owned by the
  * caller, in the layouts of rewl_state: lattice [walkers][lattice_words],
  * E [walkers], lng and H [walkers][window_bins] (updated in place);
- * win_start and lnf [windows] (read only; lnf a power of two >= 2^-39);
- * coupling_bits (+-J only, else NULL): two bit planes [right|down][L][ceil(L/32)],
- * bit set = J = -1.  stream: cudaStream_t or NULL (legacy stream); the call
- * is asynchronous on it.
+ * win_start and lnf [windows] (read only); coupling_bits (+-J only, else
+ * NULL): two bit planes [right|down][L][ceil(L/32)], bit set = J = -1.
+ * stream: cudaStream_t or NULL (legacy stream); the call is asynchronous on it.
  *
- * Working memory (walker list, status flags, sweep clock, counters) comes from
- * one fixed array of about 128 KB compiled into the library, room for
- * REWL_NOALLOC_MAX_WALKERS walkers; every GPU that loads the library keeps it
- * until the process exits.  Every call on a device uses the same array and
- * overwrites what the previous call left there (it clears what must start at
- * zero itself), so calls whose work overlaps on the GPU race: order them on
- * one stream or synchronise between them.  The first call on each device
- * looks up the array's device address; make that first call before any
- * stream capture.
+ * Inputs the kernel checks on the device, per walker: E must lie in its
+ * window (win_start[a] .. win_start[a] + window_bins - 1 in global bins) and
+ * the window's lnf must be a power of two in [2^-39, 64].  A walker that
+ * fails either is skipped (its state is left as it was) and its entry of
+ * d->status, when given, is set to REWL_EINVAL; walkers that ran get 0.
+ * d->status is an optional DEVICE array of [walkers] int32 owned by the
+ * caller, written on the stream like the state; with NULL the statuses are
+ * not reported.
+ *
+ * Working memory (walker list, internal status flags, sweep clock, counters)
+ * comes from one fixed array of about 128 KB compiled into the library, room
+ * for REWL_NOALLOC_MAX_WALKERS walkers; every GPU that loads the library
+ * keeps it until the process exits.  Every call on a device uses the same
+ * array and overwrites what the previous call left there (it clears what
+ * must start at zero itself), so calls whose work overlaps on the GPU race:
+ * order them on one stream or synchronise between them.  The first call on
+ * each device looks up the array's device address and keeps it: make that
+ * first call before any stream capture, and during set-up -- with CUDA's lazy
+ * module loading it is also the call that loads the library's device code,
+ * which the driver does with an allocation of its own.  The kept address
+ * belongs to the device's primary context; after cudaDeviceReset on that
+ * device the entry point must not be called again in the same process.
  * Errors: REWL_EINVAL (NULL pointer, bad descriptor, more than
  * REWL_NOALLOC_MAX_WALKERS walkers, window too wide for shared memory),
  * REWL_ENODEV, REWL_ECUDA.
  */
 #define REWL_NOALLOC_MAX_WALKERS 4096
 typedef struct {
-  int32_t model, q, L;                        /* as rewl_create (dim 2, periodic) */
+  int32_t model, q, L;                        /* as rewl_create (dim 2, periodic; REWL_ISING, _POTTS, _EA_PM_J) */
   int32_t windows, walkers_per_window;        /* walker W = a * walkers_per_window + k */
-  int32_t window_bins;                        /* w */
+  int32_t window_bins;                        /* w: bins of every window, and the row stride of lng and H */
   int32_t e_min, e_step;                      /* energy of global bin b = e_min + b * e_step */
   uint64_t seed;                              /* Philox key of the solve */
   uint64_t first_sweep;                       /* sweep index of the first sweep */
   int32_t sweeps;                             /* sweeps to run (>= 0) */
   int32_t lanes_per_walker;                   /* 1, 2, 4, 8, 16 or 32; 0 = 32 */
+  int32_t* status;                            /* optional device [walkers]: 0 ran, REWL_EINVAL skipped */
 } rewl_sweep_desc;
 
 rewl_status rewl_sweep_noalloc(const rewl_sweep_desc* d, uint32_t* lattice, int32_t* E, double* lng, uint32_t* H,

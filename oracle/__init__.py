@@ -169,6 +169,12 @@ class OracleREWL:
                 self._lib.orc_block_finish(self._h)
         return self._lib.orc_active_windows(self._h) == 0
 
+    def block_sweeps(self):
+        """The WL sweeps of one block (sweeps_per_exchange sweeps of every
+        walker of the windows not done) and nothing else: no clock advance, no
+        exchange, no flatness check."""
+        self._lib.orc_block_sweeps(self._h, 0, self.h * self.m)
+
     def info(self):
         a = np.zeros(16, dtype=np.int64)
         self._lib.orc_info(self._h, _ptr(a))

@@ -104,6 +104,22 @@ __device__ __forceinline__ int64_t to_fx(uint64_t V) {
   return (int64_t)(M >> (-s));
 }
 
+// ln f of a window as the exponent k of ln f = 2^-k, or kBadLnf when ln f is
+// not a power of two with -6 <= k <= 39 (the range the shadow's increment
+// 2^(40-k) and the exact repeated additions of ln g are written for; the
+// library's own windows always satisfy it: ln f0 <= 64, ln f_final >= 1e-12).
+constexpr int kBadLnf = -1000;
+__device__ __forceinline__ int lnf_exponent(double lnf) {
+  const uint64_t b = double_to_bits(lnf);
+  const int k = 1023 - (int)((b >> 52) & 0x7FF);
+  if ((b & ~(0x7FFull << 52)) != 0 || k < -6 || k > kFxBits - 1) return kBadLnf;  // sign, mantissa or range
+  return k;
+}
+
+// Per-walker status a sweep kernel leaves in DevState.status for a walker it
+// skipped (a walker is skipped only on inputs the library itself never makes).
+enum WalkerStatus : int32_t { kWalkerOk = 0, kWalkerBadInput = 1 };
+
 // Guard band of the fast acceptance test, in units of 2^-40: 2^24 units =
 // 1.5e-5 covers |logf(u) - ln u| <= 1 ulp(float) + float rounding of u
 // (< 4e-6 for ln u > -37) plus the shadow's truncation (< 1e-11).

@@ -295,6 +295,7 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   if ((prm.window_starts == nullptr) != (prm.window_widths == nullptr))
     return fail(REWL_EINVAL, "window_starts and window_widths go together");
   if (prm.prefetch_draws != 0 && prm.prefetch_draws != 1) return fail(REWL_EINVAL, "prefetch_draws %d", prm.prefetch_draws);
+  if (prm.wait_cycles < 0 || prm.wait_cycles > (1ll << 40)) return fail(REWL_EINVAL, "wait_cycles %lld", (long long)prm.wait_cycles);
   if (couplings)
     for (int64_t i = 0; i < dim * N64; ++i)
       if (couplings[i] != 1 && couplings[i] != -1) return fail(REWL_EINVAL, "coupling %lld is %d", (long long)i, couplings[i]);
@@ -534,6 +535,7 @@ static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
   A.n_active = c->n_active;
   A.wpb = c->wpb;
   A.variant = c->params.sweep_variant;
+  A.wait_cycles = c->params.wait_cycles > 0 ? c->params.wait_cycles : kDefaultWaitCycles;
   if (c->pre_on && !with_graph_capture(c)) {
     // this block's draws: prepared by the previous block (checked by its first trial index), else now
     const uint64_t t0 = c->sweep_clock * (uint64_t)c->P.N;
@@ -730,7 +732,9 @@ rewl_status rewl_set_state(rewl_handle c, const rewl_state* st) {
   const Problem& P = c->P;
   const size_t nW = P.n_walkers;
   for (int a = 0; a < P.h; ++a)
-    if (!is_pow2_double(st->lnf[a])) return fail(REWL_EINVAL, "lnf[%d] is not a power of two", a);
+    if (!is_pow2_double(st->lnf[a]) || st->lnf[a] > 64.0 || (!st->done[a] && st->lnf[a] < 0x1p-39))
+      return fail(REWL_EINVAL, "lnf[%d] = %g is not a power of two in [2^-39, 64] (or a finished window's)", a,
+                  st->lnf[a]);
   for (size_t W = 0; W < nW; ++W) {
     const int a = (int)(W / P.m);
     const int lo = P.e_min + c->win_start[a] * P.e_step, hi = lo + (c->win_width[a] - 1) * P.e_step;

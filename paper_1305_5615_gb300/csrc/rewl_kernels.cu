@@ -434,14 +434,14 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
     a = W / P.m;
     wstart = S.win_start[a];
     bin = (S.E[W] - P.e_min) / P.e_step - wstart;
-    if ((unsigned)bin >= (unsigned)window_width(P, S, a)) {
-      if (lane == 0) S.status[W] = 6;
+    kexp = lnf_exponent(S.lnf[a]);
+    if ((unsigned)bin >= (unsigned)window_width(P, S, a) || kexp == kBadLnf) {
+      if (lane == 0) S.status[W] = kWalkerBadInput;
       valid = false;
     }
   }
   if (valid) {
-    kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
-    const int64_t lnf_fx = kexp <= kFxBits ? (1ll << (kFxBits - kexp)) : 0;
+    const int64_t lnf_fx = 1ll << (kFxBits - kexp);
     int64_t fx_cur = s_fx[bin * wpb + lw];
     uint32_t h_cur = s_H[bin * wpb + lw];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
@@ -551,8 +551,8 @@ __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, Sweep
     const size_t g = (size_t)Wl * P.w + b;
     const uint32_t hs = s_H[b * wpb + l];
     const uint32_t c = hs - S.H[g];
-    if (c) {
-      const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
+    const int kx = lnf_exponent(S.lnf[Wl / P.m]);
+    if (c && kx != kBadLnf) {
       S.lng[g] = bits_to_double(add_pow2_repeated(double_to_bits(S.lng[g]), kx, c));
       S.H[g] = hs;
     }
@@ -616,7 +616,6 @@ __device__ __noinline__ bool exact_accept_fx(const DevState& S, const Problem& P
 // ---------------------------------------------------------------------------
 constexpr int kRingSlots = 4;
 constexpr size_t kRingBytes = (size_t)kRingSlots * 32 * sizeof(PreTrial) + 2 * kRingSlots * sizeof(uint64_t);
-constexpr long long kRingWaitCycles = 1ll << 34;  // ~8 s at 2 GHz; a block takes milliseconds
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -669,7 +668,8 @@ __device__ __forceinline__ PreTrial make_pretrial(const Problem& P, uint64_t t, 
 template <int MODEL, int G, bool RING = false>
 __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevState& S, uint32_t n_att, int wpb,
                                                  const int32_t* wids, int nloc, const PreTrial* pre = nullptr,
-                                                 uint32_t pre_stride = 0) {
+                                                 uint32_t pre_stride = 0,
+                                                 long long wait_cycles = kDefaultWaitCycles) {
   static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
   static_assert(!RING || G == 32, "the ring form runs one walker on one warp");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -710,7 +710,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
       const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
       const int lane = tid - 32;
       const uint32_t n_groups = (n_att + 31) / 32;
-      const long long deadline = __shfl_sync(0xffffffffu, clock64(), 0) + kRingWaitCycles;
+      const long long deadline = __shfl_sync(0xffffffffu, clock64(), 0) + wait_cycles;
       for (uint32_t g = 0; g < n_groups; ++g) {
         const uint32_t sl = g % kRingSlots, rnd = g / kRingSlots;
         if (rnd >= 1 && !mbar_wait_warp(&s_empty[sl], (rnd - 1) & 1u, deadline)) {
@@ -731,14 +731,14 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     a = W / P.m;
     wstart = S.win_start[a];
     bin = (S.E[W] - P.e_min) / P.e_step - wstart;
-    if ((unsigned)bin >= (unsigned)window_width(P, S, a)) {
-      if (lane == 0) S.status[W] = 6;
+    kexp = lnf_exponent(S.lnf[a]);
+    if ((unsigned)bin >= (unsigned)window_width(P, S, a) || kexp == kBadLnf) {
+      if (lane == 0) S.status[W] = kWalkerBadInput;
       valid = false;
     }
   }
   if (valid) {
-    kexp = 1023 - (int)((double_to_bits(S.lnf[a]) >> 52) & 0x7FF);
-    const int64_t lnf_fx = 1ll << (kFxBits - kexp);  // ln f >= 2^-39 (rewl_create checks ln f_final)
+    const int64_t lnf_fx = 1ll << (kFxBits - kexp);  // 2^-39 <= ln f <= 64 (lnf_exponent)
     int64_t* fxp = s_fx + (size_t)kGuardBins * wpb + lw;  // fxp[b * wpb] = shadow of bin b, b in [-8, w+7]
     int64_t fx_cur = fxp[bin * wpb];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
@@ -752,7 +752,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     PreTrial nxt_pre{0u, 0u, 0};
     if (my_pre && (uint32_t)lane < n_att) nxt_pre = my_pre[lane];
     long long deadline = 0;
-    if constexpr (RING) deadline = __shfl_sync(0xffffffffu, clock64(), 0) + kRingWaitCycles;
+    if constexpr (RING) deadline = __shfl_sync(0xffffffffu, clock64(), 0) + wait_cycles;
     for (uint32_t base = 0; base < n_att; base += G) {
       HotTrial tr;
       ColdTrial mv_own;  // this lane's move, written after the group if accepted
@@ -920,7 +920,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     const int Wl = wids[l];
     const size_t g = (size_t)Wl * P.w + b;
     const uint64_t v0 = double_to_bits(S.lng[g]);
-    const int kx = 1023 - (int)((double_to_bits(S.lnf[Wl / P.m]) >> 52) & 0x7FF);
+    const int kx = lnf_exponent(S.lnf[Wl / P.m]);
+    if (kx == kBadLnf) continue;  // a skipped walker: nothing ran
     const uint32_t c = (uint32_t)((s_fx[(b + kGuardBins) * wpb + l] - to_fx(v0)) >> (kFxBits - kx));
     if (c) {
       S.lng[g] = bits_to_double(add_pow2_repeated(v0, kx, c));
@@ -943,7 +944,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_chain(Problem P, DevState S, S
 // One walker per CTA of 64 threads (G = 32): warp 0 the walker, warp 1 its draws.
 template <int MODEL>
 __global__ void __launch_bounds__(64, 1) k_sweep_ring(Problem P, DevState S, SweepLaunch A) {
-  sweep_chain_body<MODEL, 32, true>(P, S, A.n_att, 1, S.active + blockIdx.x, 1);
+  sweep_chain_body<MODEL, 32, true>(P, S, A.n_att, 1, S.active + blockIdx.x, 1, nullptr, 0, A.wait_cycles);
 }
 
 // ---------------------------------------------------------------------------

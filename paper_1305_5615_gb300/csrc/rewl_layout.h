@@ -82,6 +82,10 @@ struct PreTrial {
   int64_t thr;
 };
 
+// Default bound of the ring form's hand-off waits (SM clock cycles from the
+// start of a sweep launch): about 8 s at 2 GHz, while a launch takes milliseconds.
+constexpr long long kDefaultWaitCycles = 1ll << 34;
+
 struct SweepLaunch {
   uint32_t n_att;     // trials per walker in this launch (sweeps * N); the first
                       // trial's index is clock[0] * N, read on the device
@@ -90,6 +94,7 @@ struct SweepLaunch {
   int variant;        // SweepVariant
   const PreTrial* pre;  // prepared draws [walker][pre_stride] or nullptr (drawn in the kernel)
   uint32_t pre_stride;
+  long long wait_cycles;  // ring form: bound of the hand-off waits (kDefaultWaitCycles)
 };
 
 // One request slot of the served form: the request's sizes and device

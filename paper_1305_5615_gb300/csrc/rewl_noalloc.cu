@@ -38,7 +38,8 @@ std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device; looked up once
-// per device (the host-side name of the array is only a stand-in).
+// per device (the host-side name of the array is only a stand-in) and kept
+// for the life of the process (it belongs to the device's primary context).
 rewl_status scratch_address(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return REWL_ENODEV;
@@ -52,7 +53,9 @@ rewl_status scratch_address(unsigned char** out) {
   return REWL_OK;
 }
 
-// Clears the part of the scratch a call uses and fills the walker list.
+// Clears the part of the scratch a call uses (and the caller's status array,
+// when given: S.status points there) and fills the walker list; the sweep
+// kernel marks the walkers it skips (E outside the window, ln f not usable).
 __global__ void k_noalloc_prepare(DevState S, int n_walkers, uint64_t first_sweep) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
@@ -138,7 +141,7 @@ extern "C" rewl_status rewl_sweep_noalloc(const rewl_sweep_desc* d, uint32_t* la
   unsigned char* q = base + kClockBytes;
   S.active = reinterpret_cast<int32_t*>(q);
   q += kMaxW * 4;
-  S.status = reinterpret_cast<int32_t*>(q);
+  S.status = d->status ? d->status : reinterpret_cast<int32_t*>(q);  // the caller's array, if given
   q += kMaxW * 4;
   S.wl_accept = reinterpret_cast<uint64_t*>(q);
   q += kMaxW * 8;

@@ -56,7 +56,8 @@ class rewl_params(ctypes.Structure):
                 ("walkers_per_block", ctypes.c_int32), ("mode", ctypes.c_int32), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("sweep_variant", ctypes.c_int32), ("prefetch_draws", ctypes.c_int32), ("wl_rule", ctypes.c_int32),
-                ("window_starts", ctypes.c_void_p), ("window_widths", ctypes.c_void_p)]
+                ("window_starts", ctypes.c_void_p), ("window_widths", ctypes.c_void_p),
+                ("wait_cycles", ctypes.c_int64)]
 
 
 class rewl_info(ctypes.Structure):
@@ -72,7 +73,7 @@ class rewl_sweep_desc(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("q", ctypes.c_int32), ("L", ctypes.c_int32), ("windows", ctypes.c_int32),
                 ("walkers_per_window", ctypes.c_int32), ("window_bins", ctypes.c_int32), ("e_min", ctypes.c_int32),
                 ("e_step", ctypes.c_int32), ("seed", ctypes.c_uint64), ("first_sweep", ctypes.c_uint64),
-                ("sweeps", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32)]
+                ("sweeps", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32), ("status", ctypes.c_void_p)]
 
 
 class rewl_request(ctypes.Structure):
@@ -364,7 +365,8 @@ class REWL:
                  couplings=None, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
                  entry_max_sweeps=1000, discovery_sweeps=200, timeout_ms=0, lanes_per_walker=0,
                  walkers_per_block=0, mode=MODE_PLAIN, stream=None, torch_allocator=False, profile=False,
-                 sweep_variant=-1, prefetch_draws=0, wl_rule=0, window_starts=None, window_widths=None):
+                 sweep_variant=-1, prefetch_draws=0, wl_rule=0, window_starts=None, window_widths=None,
+                 wait_cycles=0):
         if isinstance(model, str):
             model = MODELS[model]
         p = rewl_params_default()
@@ -374,6 +376,7 @@ class REWL:
         p.profile = 1 if profile else 0
         p.sweep_variant = sweep_variant
         p.prefetch_draws = prefetch_draws
+        p.wait_cycles = int(wait_cycles)
         p.wl_rule = WL_RULES[wl_rule] if isinstance(wl_rule, str) else wl_rule
         if window_starts is not None:
             self._win = (np.ascontiguousarray(window_starts, dtype=np.int32),

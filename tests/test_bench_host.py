@@ -49,7 +49,7 @@ def test_rates_microbenchmark_builds():
 
     if not (shutil.which("nvcc") or os.path.exists("/usr/local/cuda/bin/nvcc")):
         pytest.skip("no CUDA toolkit")
-    from paper_1305_5615_gb300 import ubench
+    import ubench
 
     assert os.path.exists(ubench.build())
 

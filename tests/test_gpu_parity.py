@@ -292,3 +292,20 @@ def test_prefetched_draws_match_in_kernel_draws_and_the_oracle():
     for k in ("lattice", "E", "H", "lnf", "iteration"):
         assert np.array_equal(sa[k], sb[k]), k
     assert np.array_equal(sa["lng"].view(np.uint64), sb["lng"].view(np.uint64))
+
+
+def test_ring_hand_off_wait_runs_out_and_reports_a_timeout():
+    """The ring form's bounded hand-off waits: with a bound of a few cycles
+    the first wait that finds its slot not ready gives up, both warps of every
+    walker's CTA stop, and rewl_step reports REWL_ETIMEOUT from the error word
+    at its flatness check; the context stays usable (a fresh solve then
+    matches the oracle)."""
+    D = rewl.REWL("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 0, wait_cycles=4)
+    assert D.info["sweep_variant"] == 2   # the ring form
+    with pytest.raises(rewl.RewlError) as e:
+        D.step(1000)
+    assert e.value.status == 4            # REWL_ETIMEOUT
+    assert "bounded" in rewl.rewl_last_error()
+    D.close()
+    O, D2 = make_pair("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 0)
+    _parity(O, D2, [1], "after a timed-out launch")

@@ -1,5 +1,7 @@
 // rates.cu -- microbenchmarks of the GB300 rates that bound the REWL sweep
-// kernel: FP64 add throughput and latency, double log and float logf
+// kernel: integer issue rates of the operation mixes one trial needs (the
+// Philox round's 32x32->64 multiply with a three-input XOR; the 32-bit
+// multiply, add and XOR), FP64 add throughput and latency, double log and float logf
 // throughput, Philox4x32-10 throughput (the library's own generator),
 // shared-memory load and warp-shuffle latency, and the latency of the
 // sequential WL step itself (the chain bin -> shadow loads -> 64-bit compare
@@ -10,7 +12,7 @@
 //   rate = (operations of the blocks on one SM) / (median block cycles).
 // Latencies are cycles per step of one dependent chain in one thread.
 //
-// Build and run: python -m paper_1305_5615_gb300.ubench
+// Build and run: python -m ubench
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,7 +20,7 @@
 #include <cstdio>
 #include <vector>
 
-#include "../csrc/rewl_device.cuh"
+#include "rewl_device.cuh"
 
 #define CK(x)                                                                      \
   do {                                                                             \
@@ -34,6 +36,44 @@ namespace {
 __device__ __forceinline__ void stamp(long long* cyc, long long t0) {
   __syncthreads();
   if (threadIdx.x == 0) cyc[blockIdx.x] = clock64() - t0;
+}
+
+// ---- integer mixes, 8 independent chains per thread; each step is two lane
+// operations as written (a multiply or a three-input add, then a three-input
+// XOR that feeds the next step), so nothing can be folded away:
+//   MIX 0: t = a * M (32 x 32 -> 64); a = hi(t) ^ b ^ k; b = lo(t)  -- half a Philox round
+//   MIX 1: a = (a * M) ^ b ^ k (low 32 bits); b = a + b               -- 32-bit multiply, add
+//   MIX 2: a = a + b + k; b = a ^ b ^ k                              -- add and XOR only
+template <int MIX>
+__global__ void k_int_tput(uint32_t* out, long long* cyc, int iters) {
+  uint32_t a[8], b[8];
+  for (int q = 0; q < 8; ++q) {
+    a[q] = threadIdx.x * 0x9E3779B9u + q;
+    b[q] = blockIdx.x + 0x7F4A7C15u * q;
+  }
+  const uint32_t k = 0xBB67AE85u ^ blockIdx.x, M = 0xD2511F53u;
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if constexpr (MIX == 0) {
+        const uint64_t t = (uint64_t)a[q] * M;
+        a[q] = (uint32_t)(t >> 32) ^ b[q] ^ k;
+        b[q] = (uint32_t)t;
+      } else if constexpr (MIX == 1) {
+        a[q] = (a[q] * M) ^ b[q] ^ k;
+        b[q] = a[q] + b[q];
+      } else {
+        a[q] = a[q] + b[q] + k;
+        b[q] = a[q] ^ b[q] ^ k;
+      }
+    }
+  }
+  stamp(cyc, t0);
+  uint32_t s = 0;
+  for (int q = 0; q < 8; ++q) s ^= a[q] + b[q];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 // ---- FP64 add: 8 independent chains per thread
@@ -433,6 +473,20 @@ int main() {
     return ops_per_block * bps / median(cyc);
   };
   long long one = 0;
+
+  const char* mix_names[3] = {"32x32->64 multiply + XOR3 (Philox round mix)", "32-bit multiply + XOR3, add",
+                              "add3 + XOR3"};
+  const int it_int = 1 << 12;
+  for (int mix = 0; mix < 3; ++mix) {
+    uint32_t* o = reinterpret_cast<uint32_t*>(d_out);
+    if (mix == 0) k_int_tput<0><<<blocks, threads>>>(o, d_cyc, 16);
+    if (mix == 0) k_int_tput<0><<<blocks, threads>>>(o, d_cyc, it_int);
+    if (mix == 1) k_int_tput<1><<<blocks, threads>>>(o, d_cyc, it_int);
+    if (mix == 2) k_int_tput<2><<<blocks, threads>>>(o, d_cyc, it_int);
+    CK(cudaDeviceSynchronize());
+    std::printf("integer mix %d, %-46s %8.2f lane-ops/clk/SM\n", mix, mix_names[mix],
+                per_sm_clk((double)threads * 8 * 2 * it_int));
+  }
 
   const int it_add = 1 << 14;
   k_dadd_tput<<<blocks, threads>>>(d_out, d_cyc, 16);
