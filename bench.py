@@ -52,13 +52,16 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "ising-L32-h16-m4"
 OVERLAP, FLATNESS, SPE, SPF = 0.75, 0.8, 100, 1000
 METRIC = "spin-flip attempts/s (REWL: WL sweeps + exchange + flatness/merge)"
-# Minimal integer instructions of one WL trial on the sweep kernel's path:
-# Philox4x32-10 = 10 rounds x (2 IMAD.WIDE + 2 LOP3) = 40 with the round keys
-# held in registers; site, row and column 4; neighbour loads and the dE count
-# 12; bin, window test and the fixed-point acceptance test 6; shadow, H and
-# configuration updates 4.  Total 66.
-OPS_PER_ATTEMPT = 66
-LANES_PER_SM_PER_CLK = 128   # 4 schedulers x 32 lanes
+# Integer operations of one WL trial, counted as the hardware issues them
+# (a 32x32->64 multiply and a three-input XOR are one instruction each):
+# Philox4x32-10 10 x (2 wide multiplies + 2 XOR3) = 40 and its counter 2;
+# site, row and column 3; ln u from two words (bits, convert, logf, scale,
+# convert) 10; the neighbourhood (periodic indices 8, addresses 10, five
+# loads, bit extraction 10, bond count 8) 41; energy change, bin and window
+# test 3; shadow load and the fixed-point test 7; configuration, shadow and
+# bin updates and counters 10.  About 116, in line with the 100-125 of the
+# survey's itemisation of a 2D Ising trial; 112 is used.
+OPS_PER_ATTEMPT = 112
 N_SM = 152
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_ising_L32_h16_m4.txt")
 
@@ -76,6 +79,37 @@ def kernel_source_hash():
 
 
 UBENCH_SUMMARY = os.path.join(ROOT, "profiles", "ubench_pipe_rates_and_wl_step_latency.txt")
+
+
+def measured_int_rate():
+    """The highest measured integer issue rate (lane-ops per clock per SM) of
+    the microbenchmark's integer mixes -- the Philox round's 32x32->64
+    multiply + XOR3, 32-bit multiply + XOR3 + add, add3 + XOR3 -- from the
+    committed summary; None if absent.  Taking the fastest mix as the peak
+    keeps the roofline fraction conservative."""
+    if not os.path.exists(UBENCH_SUMMARY):
+        return None
+    rates = []
+    for line in open(UBENCH_SUMMARY):
+        if line.startswith("integer mix"):
+            try:
+                rates.append(float(line.split("lane-ops")[0].split()[-1]))
+            except (IndexError, ValueError):
+                pass
+    return max(rates) if rates else None
+
+
+def measured_philox_rate():
+    """Measured Philox4x32-10 calls per clock per SM (microbenchmark summary)."""
+    if not os.path.exists(UBENCH_SUMMARY):
+        return None
+    for line in open(UBENCH_SUMMARY):
+        if line.startswith("Philox4x32-10"):
+            try:
+                return float(line.split("calls/clk/SM")[0].split()[-1])
+            except (IndexError, ValueError):
+                return None
+    return None
 
 
 def isolated_step_cycles():
@@ -439,17 +473,25 @@ def run_gb300(args, wl, world, rank, local):
 
     # ---- end to end through the C ABI with host buffers: create (H2D of the
     # problem), one flatness period, the joined ln g read back (D2H), destroy
-    e2e_times, h2d, d2h, e2e_att = [], [], [], 0
+    e2e_times, h2d, d2h, e2e_att, parts = [], [], [], 0, []
     for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)          # same L2 state as the device-timed steps
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         E = make()
+        t1 = time.perf_counter()
         E.step(SPF)
+        t2 = time.perf_counter()
         g, e0, de = E.lng()
         inf = rewl.rewl_get_info(E._h)   # counters include the ln g read-back
+        t3 = time.perf_counter()
         E.close()
         torch.cuda.synchronize()
-        e2e_times.append(time.perf_counter() - t0)
+        t4 = time.perf_counter()
+        e2e_times.append(t4 - t0)
+        parts.append((t1 - t0, t2 - t1, t3 - t2, t4 - t3))
         h2d.append(inf["h2d_bytes"])
         d2h.append(inf["d2h_bytes"])
         e2e_att += inf["attempts"]
@@ -457,7 +499,13 @@ def run_gb300(args, wl, world, rank, local):
     if e2e_times:
         e2e = {"value": e2e_att / sum(e2e_times), "unit": "attempts/s",
                "h2d_bytes_per_step": int(statistics.mean(h2d)), "d2h_bytes_per_step": int(statistics.mean(d2h)),
-               "step": "rewl_create + rewl_step(1000 sweeps) + rewl_get_lng + rewl_destroy, host buffers"}
+               "step": "rewl_create (H2D of the problem, entry walks) + rewl_step(1000 sweeps: the first flatness "
+                       "period of a fresh solve, sweeps 0-1000) + rewl_get_lng (D2H and the host join) + "
+                       "rewl_destroy, host buffers, L2 flushed before each step",
+               "ms_per_step": {"create": 1e3 * statistics.mean(p[0] for p in parts),
+                               "sweeps": 1e3 * statistics.mean(p[1] for p in parts),
+                               "read_back": 1e3 * statistics.mean(p[2] for p in parts),
+                               "destroy": 1e3 * statistics.mean(p[3] for p in parts)}}
 
     # ---- roofline of the dominant kernel (the sweep kernel)
     peaks = measured_peaks()
@@ -467,21 +515,32 @@ def run_gb300(args, wl, world, rank, local):
         att_per_launch = att_local / launches
         avg_s = sweep_ms / launches / 1e3
         achieved = att_per_launch * OPS_PER_ATTEMPT / avg_s / 1e12
-        peak = N_SM * LANES_PER_SM_PER_CLK * f_max / 1e12
+        rate = measured_int_rate()
+        peak = N_SM * (rate or 128.0) * f_max / 1e12
         traffic = traffic_from_profile(args.workload, i1["sweep_variant"])
+        names = {0: "k_sweep_chain", 1: "k_sweep_spec", 2: "k_sweep_ring", 3: "k_sweep_lane"}
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_sweep", "avg_launch_ms": avg_s * 1e3,
+                "traffic": traffic, "kernel": names.get(i1["sweep_variant"], "k_sweep"), "avg_launch_ms": avg_s * 1e3,
                 "attempts_per_launch": att_per_launch, "ops_per_attempt": OPS_PER_ATTEMPT,
-                "peak_basis": "152 SMs x 128 int lanes/clk x %.0f MHz (derived from unit counts and the maximum SM clock)" % (f_max / 1e6),
+                "peak_basis": ("measured: %.1f integer lane-ops/clk/SM (the fastest integer mix of ubench/rates.cu, "
+                               "profiles/ubench_pipe_rates_and_wl_step_latency.txt) x 152 SMs x %.0f MHz"
+                               % (rate, f_max / 1e6)) if rate else
+                              "derived: 152 SMs x 128 int lanes/clk x %.0f MHz (no microbenchmark summary)" % (f_max / 1e6),
                 "sweep_share_of_step": sweep_ms / 1e3 / t_local if t_local > 0 else None}
+        ph = measured_philox_rate()
+        if ph:   # every trial needs one Philox4x32-10 call: a bound of its own
+            roof["philox_bound_attempts_per_s"] = ph * N_SM * f_max
+            roof["frac_of_philox_bound"] = att_per_launch / avg_s / (ph * N_SM * f_max)
         iso = isolated_step_cycles()
         f_run = (clocks or {}).get("sm_mhz") or f_max / 1e6
         cyc = avg_s * f_run * 1e6 / (SPE * sites(wl))  # per trial of one walker (all walkers run at once)
-        if iso is not None and args.workload == DEFAULT_WORKLOAD:
+        if iso is not None:
+            walkers = att_per_launch / (SPE * sites(wl))
             roof["latency"] = {"unit": "clk/trial per walker", "kernel": cyc, "isolated_step": iso,
-                               "frac": iso / cyc, "sm_mhz": f_run,
+                               "frac": iso / cyc, "sm_mhz": f_run, "walkers": walkers,
+                               "chain_bound_attempts_per_s": walkers * f_run * 1e6 / iso,
                                "basis": "the sequential WL step alone (dependency chain only), measured by "
-                                        "ubench/rates.cu on the GB300"}
+                                        "ubench/rates.cu on the GB300; bound = walkers x SM clock / its cycles"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -499,6 +558,12 @@ def run_gb300(args, wl, world, rank, local):
                                           "%.1f s of whole exchange blocks at the same time" % (
                                               P, what, seed, seed + P - 1, el_p)}
 
+    tdos = None
+    if rank == 0 and world == 1 and args.workload == DEFAULT_WORKLOAD and not args.no_tdos:
+        # the metric's second half: time to the converged ln g, served vs plain, p50/p99
+        tdos = {"ising-L8-h4-m2": tdos_record(rewl, WORKLOADS["ising-L8-h4-m2"], list(range(32)), _exact_ising(8)),
+                "ising-L32-h16-m4": tdos_record(rewl, WORKLOADS["ising-L32-h16-m4"], list(range(8)), _exact_ising(32))}
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -514,7 +579,8 @@ def run_gb300(args, wl, world, rank, local):
                            "automatic (sweep_variant %d)" % i1["sweep_variant"]},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": args.steps * (3 * (SPF // SPE) + 1), "clocks": clocks,
-                "solve_state": {"sweep_clock": i1["sweep_clock"], "windows_done": i1["windows_done"]}}
+                "solve_state": {"sweep_clock": i1["sweep_clock"], "windows_done": i1["windows_done"]},
+                "time_to_dos": tdos}
         print(json.dumps(line), flush=True)
 
 
@@ -719,22 +785,128 @@ def run_windows_balance(args, world, rank, local):
                           "per_seed_slowest_sweeps_equal_balanced": runs, "detail": out}), flush=True)
 
 
-def _exact_ising_L32():
-    """ln g of the exact 32 x 32 Ising DOS (tests/golden, written from the
-    Kaufman/Beale closed form), indexed by global bin."""
+def _exact_ising(L):
+    """ln g of the exact L x L Ising DOS (tests/golden, written from the
+    Kaufman/Beale closed form), indexed by global bin (E = -2N + 4 b); -inf
+    for levels that do not exist."""
     import math
 
     import numpy as np
 
-    out = np.full(1025, -np.inf)
-    for line in open(os.path.join(ROOT, "tests", "golden", "ising_L32_exact_dos.txt")):
+    N = L * L
+    out = np.full(N + 1, -np.inf)
+    for line in open(os.path.join(ROOT, "tests", "golden", "ising_L%d_exact_dos.txt" % L)):
         if line.startswith("#"):
             continue
         e, c = line.split()
         c = int(c)
+        if c == 0:
+            continue
         b = c.bit_length()
-        out[(int(e) + 2048) // 4] = math.log(c) if b < 1000 else math.log(c >> (b - 60)) + (b - 60) * math.log(2.0)
+        out[(int(e) + 2 * N) // 4] = math.log(c) if b < 1000 else math.log(c >> (b - 60)) + (b - 60) * math.log(2.0)
     return out
+
+
+def _exact_ising_L32():
+    return _exact_ising(32)
+
+
+def dos_accuracy(g, e0, de, lnx):
+    """Max relative error |ln g - ln g_exact| / ln g_exact of each half of the
+    estimate normalised at its own end (E <= 0 with g(E_min) = 2, E >= 0 with
+    g(E_max) = 2), and the max absolute deviation after the best shift."""
+    import numpy as np
+
+    fin = np.isfinite(lnx)
+    E = e0 + de * np.arange(len(g))
+    lo, hi = fin & (E <= 0), fin & (E >= 0)
+    top = np.nonzero(fin)[0][-1]
+    g_lo, g_hi = g - g[0] + lnx[0], g - g[top] + lnx[top]
+    d = g[fin] - lnx[fin]
+    return {"max_rel_err_E_le_0": float(np.max(np.abs(g_lo[lo] - lnx[lo]) / lnx[lo])),
+            "max_rel_err_E_ge_0": float(np.max(np.abs(g_hi[hi] - lnx[hi]) / lnx[hi])),
+            "max_abs_err_best_shift": float(np.max(np.abs(d - d.mean())))}
+
+
+def tdos_record(rewl, wl, seeds, exact=None, alone=True):
+    """Time to the converged ln g (every window at ln f_final), measured three
+    ways on the same seeds, each from submission / creation to the result:
+      served  -- all seeds submitted at once to the request server (continuous
+                 batching: one fused launch per phase for all requests);
+      plain, concurrent -- one rewl_create + rewl_step(to completion) +
+                 rewl_get_lng handle per seed, each on its own stream driven by
+                 its own host thread, all started together (one launch per
+                 phase per solve);
+      plain, alone -- the first seed solved by itself on the GPU.
+    p50/p99 over the seeds, the served results checked bit for bit against the
+    plain ones, and (exact DOS given) each seed's error against it."""
+    import numpy as np
+
+    rec = {"seeds": list(seeds), "lnf_final": wl["lnf_final"]}
+    # ---- served
+    S = rewl.RewlServer(device_bytes=8 << 30, max_running=len(seeds))
+    t0 = time.perf_counter()
+    ids = [S.submit(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], sd, q=wl["q"])
+           for sd in seeds]
+    while True:
+        st = S.run(1)
+        if st["running"] == 0 and st["queued"] == 0:
+            break
+    wall = time.perf_counter() - t0
+    lat, sweeps, served_g = [], [], []
+    for rid in ids:
+        inf = S.poll(rid)
+        assert inf["state"] == rewl.REQ_DONE, inf
+        lat.append(inf["latency_ms"] / 1e3)
+        sweeps.append(int(inf["sweeps"]))
+        served_g.append(S.result(rid))
+    rec["served"] = {"wall_s": wall, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                     "per_seed_s": lat, "attempts_per_s": st["attempts"] / wall}
+    rec["sweeps_to_converge"] = sweeps
+    S.close()
+
+    # ---- plain, concurrent
+    res = [None] * len(seeds)
+    start = threading.Barrier(len(seeds), timeout=600.0)
+
+    def solve(k):
+        start.wait()
+        t1 = time.perf_counter()
+        D = rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seeds[k], q=wl["q"])
+        D.step(0)
+        g = D.lng()
+        res[k] = (time.perf_counter() - t1, g, int(D.info["attempts"]), int(D.info["sweep_clock"]))
+        D.close()
+
+    t0 = time.perf_counter()
+    _run_threads(solve, len(seeds))
+    wall = time.perf_counter() - t0
+    pl = [r[0] for r in res]
+    rec["plain_concurrent"] = {"wall_s": wall, "p50_s": float(np.percentile(pl, 50)),
+                               "p99_s": float(np.percentile(pl, 99)), "per_seed_s": pl,
+                               "attempts_per_s": sum(r[2] for r in res) / wall}
+    rec["bit_identical_served_vs_plain"] = all(
+        np.array_equal(r[1][0].view(np.uint64), g[0].view(np.uint64)) for r, g in zip(res, served_g))
+    rec["sweeps_equal_served_vs_plain"] = [r[3] for r in res] == sweeps
+    # ---- plain, alone
+    if alone:
+        t1 = time.perf_counter()
+        D = rewl.REWL(wl["model"], wl["L"], wl["h"], OVERLAP, wl["m"], FLATNESS, wl["lnf_final"], seeds[0], q=wl["q"])
+        D.step(0)
+        D.lng()
+        rec["plain_alone"] = {"seed": seeds[0], "s": time.perf_counter() - t1,
+                              "attempts_per_s": D.info["attempts"] / (time.perf_counter() - t1)}
+        D.close()
+    if exact is not None:
+        acc = [dos_accuracy(g, e0, de, exact) for g, e0, de in served_g]
+        rec["accuracy_vs_exact"] = {
+            "per_seed": acc,
+            "worst_max_rel_err_E_le_0": max(a["max_rel_err_E_le_0"] for a in acc),
+            "worst_max_rel_err_E_ge_0": max(a["max_rel_err_E_ge_0"] for a in acc),
+            "seeds_within_2e-3": sum(1 for a in acc if max(a["max_rel_err_E_le_0"], a["max_rel_err_E_ge_0"]) <= 2e-3),
+            "mean_of_seeds": dos_accuracy(np.mean([g for g, _, _ in served_g], axis=0), served_g[0][1],
+                                          served_g[0][2], exact)}
+    return rec
 
 
 def run_rule_compare(args, world, rank, local):
@@ -927,6 +1099,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tdos", action="store_true",
+                    help="skip the time-to-DOS records (served vs plain) of the default workload")
     ap.add_argument("--cpu-all-cores", type=int, default=1,
                     help="also time one oracle solve per host core at the same time (0 = single core only)")
     ap.add_argument("--tdos-oracle-limit", type=float, default=300.0,

@@ -100,7 +100,10 @@ typedef struct {
                                     per block are not forced, else the chain form), REWL_SWEEP_CHAIN
                                     (two-deep chain), REWL_SWEEP_STAGED (staged one-deep chain),
                                     REWL_SWEEP_RING (the chain with its draws made by a second, producer warp
-                                    of the CTA; 32 lanes and one walker per CTA) */
+                                    of the CTA; 32 lanes and one walker per CTA), REWL_SWEEP_LANE (one walker
+                                    per thread, walkers_per_warp walkers in each warp; lanes_per_walker must
+                                    be 0 or 1, walkers_per_block is then the walkers of a CTA, a multiple of
+                                    walkers_per_warp, at most 8 warps) */
   int32_t prefetch_draws;        /* 1 = in plain mode with variant 0 the draws of the next block (sites,
                                     ln u, conflict masks) are prepared on a second stream while the current
                                     block runs, when both buffers fit in 1 GiB; 0 = no (default: kernels
@@ -118,6 +121,8 @@ typedef struct {
                                     launch; 0 = 2^34 (about 8 s at 2 GHz, while a launch takes
                                     milliseconds).  When a wait runs out both warps stop early and
                                     rewl_step returns REWL_ETIMEOUT at its next flatness check */
+  int32_t walkers_per_warp;      /* REWL_SWEEP_LANE: walkers per warp, 1..32 (lanes past it idle); 0 = as
+                                    few as spread the walkers over every SM sub-partition */
 } rewl_params;
 
 /*
@@ -135,7 +140,7 @@ typedef struct {
  * ln f < lnf_final.
  */
 enum { REWL_RULE_FLAT = 0, REWL_RULE_ONE_OVER_T = 1 };
-enum { REWL_SWEEP_AUTO = -1, REWL_SWEEP_CHAIN = 0, REWL_SWEEP_STAGED = 1, REWL_SWEEP_RING = 2 };
+enum { REWL_SWEEP_AUTO = -1, REWL_SWEEP_CHAIN = 0, REWL_SWEEP_STAGED = 1, REWL_SWEEP_RING = 2, REWL_SWEEP_LANE = 3 };
 
 /* Fills *p with the defaults above. */
 void rewl_params_default(rewl_params* p);
@@ -227,7 +232,8 @@ typedef struct {
   int64_t h2d_bytes;         /* bytes copied host -> device by this handle so far */
   int64_t d2h_bytes;         /* bytes copied device -> host by this handle so far */
   int32_t prefetch_draws;    /* 1 when the next block's draws are prepared on a second stream */
-  int32_t sweep_variant;     /* the sweep form in use (REWL_SWEEP_CHAIN, _STAGED or _RING) */
+  int32_t sweep_variant;     /* the sweep form in use (REWL_SWEEP_CHAIN, _STAGED, _RING or _LANE) */
+  int32_t walkers_per_warp;  /* REWL_SWEEP_LANE: walkers per warp (else 0) */
 } rewl_info;
 
 rewl_status rewl_get_info(rewl_handle h, rewl_info* info);
@@ -285,14 +291,16 @@ rewl_status rewl_get_state(rewl_handle h, rewl_state* st);
 /*
  * rewl_autotune -- picks the sweep kernel's launch shape for one problem by
  * timing candidates on the problem itself: the ring form (32 lanes and a
- * producer warp per walker) and the chain form with 32, 16, 8, 4 and 2 lanes
- * per walker (walkers per CTA as rewl_create chooses).  Each candidate is a
+ * producer warp per walker), the chain form with 32, 16, 8, 4 and 2 lanes
+ * per walker (walkers per CTA as rewl_create chooses) and the lane form with
+ * the walkers spread over every SM sub-partition or 1, 2, 4, 8, 16 and 32
+ * walkers per warp.  Each candidate is a
  * fresh rewl_create with the given arguments, one warm-up block, then `sweeps`
  * sweeps timed with CUDA events around every sweep launch.  All candidates
  * compute the same bits.  results: caller array of `capacity` entries, one per
  * candidate tried (*n_results); *best: `params` (or the defaults) with
- * sweep_variant, lanes_per_walker and walkers_per_block of the fastest, ready
- * for rewl_create.  Errors: REWL_EINVAL (arguments, sweeps not a multiple of
+ * sweep_variant, lanes_per_walker, walkers_per_block and walkers_per_warp of
+ * the fastest, ready for rewl_create.  Errors: REWL_EINVAL (arguments, sweeps not a multiple of
  * sweeps_per_exchange, no candidate ran); a candidate's own failure is in its
  * result's status.
  */
@@ -301,6 +309,7 @@ typedef struct {
   int32_t status;           /* rewl_status of the candidate's run */
   double ms_per_launch;     /* mean device time of one sweep launch (sweeps_per_exchange sweeps) */
   double attempts_per_s;    /* trials per second of sweep-kernel time */
+  int32_t walkers_per_warp; /* the lane form's walkers per warp (else 0) */
 } rewl_tune_result;
 
 rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice* lattice, const int8_t* couplings,

@@ -8,7 +8,7 @@ from paper_1305_5615_gb300 import rewl
 
 def make_pair(model, L, h, o, m, flatness, lnf_final, seed, q=2, couplings=None, spe=100, spf=1000, lnf0=1.0,
               G=0, wpb=0, mode=rewl.MODE_PLAIN, entry_max_sweeps=1000, discovery_sweeps=200, wl_rule="flat",
-              window_starts=None, window_widths=None):
+              window_starts=None, window_widths=None, **gpu_kw):
     O = OracleREWL(model, L, h, o, m, flatness, lnf_final, seed, q=q, couplings=couplings, sweeps_per_exchange=spe,
                    sweeps_per_flat_check=spf, lnf0=lnf0, entry_max_sweeps=entry_max_sweeps,
                    discovery_sweeps=discovery_sweeps, wl_rule=wl_rule, window_starts=window_starts,
@@ -16,7 +16,7 @@ def make_pair(model, L, h, o, m, flatness, lnf_final, seed, q=2, couplings=None,
     D = rewl.REWL(model, L, h, o, m, flatness, lnf_final, seed, q=q, couplings=couplings, sweeps_per_exchange=spe,
                   sweeps_per_flat_check=spf, lnf0=lnf0, entry_max_sweeps=entry_max_sweeps,
                   discovery_sweeps=discovery_sweeps, lanes_per_walker=G, walkers_per_block=wpb, mode=mode,
-                  wl_rule=wl_rule, window_starts=window_starts, window_widths=window_widths)
+                  wl_rule=wl_rule, window_starts=window_starts, window_widths=window_widths, **gpu_kw)
     return O, D
 
 
