@@ -518,7 +518,7 @@ def run_gb300(args, wl, world, rank, local):
         rate = measured_int_rate()
         peak = N_SM * (rate or 128.0) * f_max / 1e12
         traffic = traffic_from_profile(args.workload, i1["sweep_variant"])
-        names = {0: "k_sweep_chain", 1: "k_sweep_spec", 2: "k_sweep_ring", 3: "k_sweep_lane"}
+        names = {0: "k_sweep_chain", 1: "k_sweep_spec", 2: "k_sweep_ring"}
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": names.get(i1["sweep_variant"], "k_sweep"), "avg_launch_ms": avg_s * 1e3,
                 "attempts_per_launch": att_per_launch, "ops_per_attempt": OPS_PER_ATTEMPT,
@@ -602,23 +602,6 @@ def served_requests(n, seed):
     return out
 
 
-def _plain_sweep_seconds(rewl, shapes, seed):
-    """Plain form, per request shape: device seconds per sweep of a request of
-    that shape alone (8 windows x 4 walkers, all windows running), and the
-    seconds of rewl_create.  2000 sweeps after 1000 of warm-up."""
-    out = {}
-    for model, L, q in shapes:
-        t0 = time.perf_counter()
-        D = rewl.REWL(model, L, 8, OVERLAP, 4, FLATNESS, 1e-6, seed, q=q)
-        t_create = time.perf_counter() - t0
-        D.step(1000)
-        t1 = time.perf_counter()
-        D.step(2000)
-        out[(model, L)] = ((time.perf_counter() - t1) / 2000.0, t_create)
-        D.close()
-    return out
-
-
 def _fifo_latencies(arrivals, services):
     """One server, first come first served: latency of each job (Lindley)."""
     free_at, lat = 0.0, []
@@ -629,33 +612,63 @@ def _fifo_latencies(arrivals, services):
     return lat
 
 
-def run_served(args, world, rank, local):
-    """A stream of DOS requests through the request server (continuous
-    batching, shape groups on their own streams): p50/p99 latency from arrival
-    to result and aggregate attempts/s, measured.  Beside it the plain form
-    (one request at a time, one launch per phase): its service time per
-    request is the request's own sweep count (the same in both forms -- the
-    trajectories are bit-identical) times the plain seconds per sweep of its
-    shape, measured here per shape, and its latencies follow from the same
-    arrivals through a first-come-first-served queue.  --plain-check requests
-    are also solved plain in full, to check the result bits and the modelled
-    service time."""
-    import numpy as np
-    import torch
+def _plain_request(rewl, r):
+    """One request solved in plain form on its own handle (and stream):
+    rewl_create + rewl_step to completion + rewl_get_lng.  Returns (ln g,
+    attempts)."""
+    D = rewl.REWL(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"])
+    D.step(0)
+    g = D.lng()[0]
+    att = int(D.info["attempts"])
+    D.close()
+    return g, att
 
-    torch.cuda.set_device(local)
-    from paper_1305_5615_gb300 import rewl
 
-    reqs = served_requests(args.requests, args.seed)
-    if args.mix != "mixed":  # one shape only, e.g. "ising:32"
-        model, L = args.mix.split(":")
-        reqs = [dict(model=model, L=int(L), q=10 if model == "potts" else 2, seed=i) for i in range(len(reqs))]
-    rng = np.random.default_rng(args.seed + 1)
-    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=len(reqs))) if args.rate > 0 else np.zeros(len(reqs))
-    S = rewl.RewlServer(device_bytes=args.server_gb << 30, max_running=args.slots)
+def run_plain_stream(rewl, reqs, arrivals, concurrency):
+    """The plain form over a stream: every request is solved by its own
+    rewl_create/rewl_step handle on its own stream, started at its arrival by
+    a host thread, at most `concurrency` at once (first come first served
+    beyond that).  Returns per-request latency (arrival -> result), ln g,
+    attempts, and the wall time."""
+    n = len(reqs)
+    sem = threading.Semaphore(concurrency)
+    lat, res = [None] * n, [None] * n
+    err = []
+    t0 = time.perf_counter()
+
+    def run(k):
+        try:
+            with sem:
+                res[k] = _plain_request(rewl, reqs[k])
+            lat[k] = time.perf_counter() - t0 - arrivals[k]
+        except BaseException as e:
+            err.append(e)
+
+    threads = []
+    for k in range(n):
+        delay = arrivals[k] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        th = threading.Thread(target=run, args=(k,))
+        th.start()
+        threads.append(th)
+    for th in threads:
+        th.join()
+    if err:
+        raise RuntimeError("plain solve failed: %r" % (err[0],))
+    return lat, res, time.perf_counter() - t0
+
+
+def run_served_stream(rewl, reqs, arrivals, slots, server_gb, timeout_s):
+    """The served form over a stream: each request submitted at its arrival
+    to one request server (continuous batching).  Returns per-request latency
+    (arrival -> result; None if unfinished), ln g, attempts, wall time and
+    the server's rounds."""
+    S = rewl.RewlServer(device_bytes=server_gb << 30, max_running=slots)
     ids, t_sub = [], []
     t0 = time.perf_counter()
     nxt = 0
+    st = {"rounds": 0}
     while True:
         now = time.perf_counter() - t0
         while nxt < len(reqs) and arrivals[nxt] <= now:
@@ -666,65 +679,98 @@ def run_served(args, world, rank, local):
         st = S.run(1)
         if nxt == len(reqs) and st["running"] == 0 and st["queued"] == 0:
             break
-        if args.served_timeout > 0 and time.perf_counter() - t0 > args.served_timeout:
+        if timeout_s > 0 and time.perf_counter() - t0 > timeout_s:
             break
         if st["running"] == 0 and st["queued"] == 0 and nxt < len(reqs):
             time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
-    t_end = time.perf_counter() - t0
-    done, att, n_failed, n_open = [], 0, 0, 0
+    wall = time.perf_counter() - t0
+    lat, res = [], []
     for k, rid in enumerate(ids):
         inf = S.poll(rid)
-        att += inf["attempts"]
         if inf["state"] == rewl.REQ_DONE:
-            done.append((k, 1e-3 * (1e3 * (t_sub[k] - arrivals[k]) + inf["latency_ms"]), inf["sweeps"], inf["attempts"]))
-        elif inf["state"] == rewl.REQ_FAILED:
-            n_failed += 1
+            lat.append(t_sub[k] - arrivals[k] + inf["latency_ms"] / 1e3)
+            res.append((S.result(rid)[0], int(inf["attempts"])))
         else:
-            n_open += 1
-    lat = np.array([d[1] for d in done]) if done else np.zeros(1)
-    served = {"requests": len(reqs), "submitted": len(ids), "completed": len(done), "failed": n_failed,
-              "unfinished_at_stop": n_open, "wall_s": t_end, "attempts": att, "attempts_per_s": att / t_end,
-              "completed_per_s": len(done) / t_end, "p50_latency_s": float(np.percentile(lat, 50)),
-              "p99_latency_s": float(np.percentile(lat, 99)), "rate_per_s": args.rate, "slots": args.slots,
-              "rounds": st["rounds"]}
+            lat.append(None)
+            res.append((None, int(inf["attempts"])))
+    lat += [None] * (len(reqs) - len(ids))
+    res += [(None, 0)] * (len(reqs) - len(ids))
+    S.close()
+    return lat, res, wall, st["rounds"]
 
-    # ---- plain form: per-shape sweep time, modelled service times, FIFO over the same arrivals
-    shapes = sorted({(r["model"], r["L"], r["q"]) for r in reqs})
-    per = _plain_sweep_seconds(rewl, shapes, args.seed)
+
+def _summary(lat, res, wall):
+    import numpy as np
+
+    done = [x for x in lat if x is not None]
+    att = sum(r[1] for r in res)
+    return {"completed": len(done), "unfinished": len(lat) - len(done), "wall_s": wall,
+            "attempts_per_s": att / wall, "completed_per_s": len(done) / wall,
+            "p50_latency_s": float(np.percentile(done, 50)) if done else None,
+            "p99_latency_s": float(np.percentile(done, 99)) if done else None}
+
+
+def run_served(args, world, rank, local):
+    """A stream of DOS requests, served form against plain form, both measured.
+
+    Plain form: every request solved by its own handle (one launch per phase,
+    its own stream), up to --slots at once.  Calibration (--rate < 0): a
+    backlog of --calib-requests requests of the mix through the plain form
+    gives its capacity C (requests completed per second); the stream then
+    arrives as a Poisson process at rate lambda = -rate x C (0.8 x C for
+    --rate -0.8).  The same arrivals go through the request server (served)
+    and through the plain form; p50/p99 latency from arrival to result,
+    aggregate attempts/s, and every request's ln g compared bit for bit
+    between the two."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_1305_5615_gb300 import rewl
+
+    rewl.load()
+    reqs = served_requests(args.requests, args.seed)
+    if args.mix != "mixed":  # one shape only, e.g. "ising:32"
+        model, L = args.mix.split(":")
+        reqs = [dict(model=model, L=int(L), q=10 if model == "potts" else 2, seed=i) for i in range(len(reqs))]
+    calib = None
+    rate = args.rate
+    if rate < 0:
+        creq = served_requests(args.calib_requests, args.seed + 1000)
+        for i, r in enumerate(creq):
+            r["seed"] = 100000 + i
+        clat, cres, cwall = run_plain_stream(rewl, creq, [0.0] * len(creq), args.slots)
+        cap = len(creq) / cwall
+        rate = -args.rate * cap
+        calib = {"requests": len(creq), "concurrency": args.slots, "wall_s": cwall,
+                 "plain_capacity_requests_per_s": cap, "load_factor": -args.rate, "rate_per_s": rate}
+    rng = np.random.default_rng(args.seed + 1)
+    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))) if rate > 0 else [0.0] * len(reqs)
+    slat, sres, swall, srounds = run_served_stream(rewl, reqs, arrivals, args.slots, args.server_gb,
+                                                   args.served_timeout)
+    served = _summary(slat, sres, swall)
+    served["rounds"] = srounds
     plain = None
-    if done:
-        svc = [per[(reqs[k]["model"], reqs[k]["L"])][0] * sw + per[(reqs[k]["model"], reqs[k]["L"])][1]
-               for k, _, sw, _ in done]
-        plat = np.array(_fifo_latencies([arrivals[k] for k, _, _, _ in done], svc))
-        plain = {"completed_requests_modelled": len(done), "service_s_mean": float(np.mean(svc)),
-                 "busy_s": float(np.sum(svc)), "attempts_per_s": float(sum(d[3] for d in done) / np.sum(svc)),
-                 "p50_latency_s": float(np.percentile(plat, 50)), "p99_latency_s": float(np.percentile(plat, 99)),
-                 "sweep_ms_by_shape": {"%s-L%d" % k: 1e3 * v[0] for k, v in per.items()}}
-    # ---- live plain solves of the cheapest completed requests: result bits and modelled time
-    check = []
-    for k, _, sw, _ in sorted(done, key=lambda d: per[(reqs[d[0]]["model"], reqs[d[0]]["L"])][0] * d[2])[:args.plain_check]:
-        r = reqs[k]
-        t1 = time.perf_counter()
-        D = rewl.REWL(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"])
-        D.step(0)
-        g, _, _ = D.lng()
-        el = time.perf_counter() - t1
-        gs, _, _ = S.result(ids[k])
-        check.append({"shape": "%s-L%d" % (r["model"], r["L"]), "sweeps": sw, "plain_s": el,
-                      "modelled_s": per[(r["model"], r["L"])][0] * sw + per[(r["model"], r["L"])][1],
-                      "bit_identical": bool(np.array_equal(g.view(np.uint64), gs.view(np.uint64)))})
-        D.close()
-    if plain is not None:
-        plain["live_check"] = check
+    same = None
+    if not args.no_plain:
+        plat, pres, pwall = run_plain_stream(rewl, reqs, arrivals, args.slots)
+        plain = _summary(plat, pres, pwall)
+        same = all(sg is None or np.array_equal(sg.view(np.uint64), pg.view(np.uint64))
+                   for (sg, _), (pg, _) in zip(sres, pres))
     if rank == 0:
-        print(json.dumps({"metric": "served DOS requests: aggregate spin-flip attempts/s; p50/p99 arrival->result",
+        print(json.dumps({"metric": "served DOS requests: p50/p99 arrival->result and aggregate spin-flip attempts/s, "
+                                    "served vs plain",
                           "value": served["attempts_per_s"], "unit": "attempts/s", "n_gpus": world,
                           "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "served-stream", "desc": "+-J L in {12,16,20,24,32} (p=1/2 couplings "
-                                     "from the request seed), Ising and Potts q=10 L in {16,24,32}, 1/3 each; 8 windows "
-                                     "x 4 walkers; ln f -> 1e-6; arrivals %s" % (
-                                         "Poisson %.4g/s" % args.rate if args.rate > 0 else "all at t=0 (backlog)")},
-                          "served": served, "plain_one_at_a_time": plain}), flush=True)
+                          "config": {"workload": "served-stream", "requests": len(reqs),
+                                     "desc": "+-J L in {12,16,20,24,32} (p=1/2 couplings from the request seed), "
+                                             "Ising and Potts q=10 L in {16,24,32}, 1/3 each; 8 windows x 4 walkers; "
+                                             "ln f -> 1e-6; arrivals %s" % (
+                                                 "Poisson %.4g/s" % rate if rate > 0 else "all at t=0 (backlog)"),
+                                     "slots": args.slots, "plain": "one handle per request on its own stream, up to "
+                                                                   "%d at once" % args.slots},
+                          "calibration": calib, "served": served, "plain": plain,
+                          "results_bit_identical_served_vs_plain": same}), flush=True)
 
 
 def _first_iteration(rewl, wl, seed, max_sweeps, **kw):
@@ -1106,11 +1152,15 @@ def main():
     ap.add_argument("--tdos-oracle-limit", type=float, default=300.0,
                     help="time-to-dos: solve the seeds with the oracle in full if each takes less than this (s)")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch shapes first (rewl_autotune)")
-    ap.add_argument("--requests", type=int, default=192, help="served-stream: number of requests")
-    ap.add_argument("--rate", type=float, default=0.0, help="served-stream: Poisson arrivals per second (0 = all at once)")
-    ap.add_argument("--slots", type=int, default=96, help="served-stream: request slots")
+    ap.add_argument("--requests", type=int, default=100, help="served-stream: number of requests")
+    ap.add_argument("--rate", type=float, default=-0.8,
+                    help="served-stream: Poisson arrivals per second; 0 = all at once; < 0: -rate x the plain "
+                         "form's capacity measured in a calibration run first")
+    ap.add_argument("--calib-requests", type=int, default=64, help="served-stream: calibration backlog")
+    ap.add_argument("--no-plain", action="store_true", help="served-stream: skip the plain arm")
+    ap.add_argument("--slots", type=int, default=256, help="served-stream: request slots (served) and the "
+                                                          "plain form's concurrent handles")
     ap.add_argument("--server-gb", type=int, default=64, help="served-stream: device-memory budget in GiB")
-    ap.add_argument("--plain-check", type=int, default=3, help="served-stream: solve this many plain in full")
     ap.add_argument("--mix", default="mixed", help="served-stream: 'mixed', or one shape as model:L (e.g. ising:32)")
     ap.add_argument("--served-timeout", type=float, default=1200.0, help="served-stream: stop after this many seconds")
     ap.add_argument("--base-workload", default="potts-q10-L32-h32-m16", choices=sorted(WORKLOADS),

@@ -100,10 +100,7 @@ typedef struct {
                                     per block are not forced, else the chain form), REWL_SWEEP_CHAIN
                                     (two-deep chain), REWL_SWEEP_STAGED (staged one-deep chain),
                                     REWL_SWEEP_RING (the chain with its draws made by a second, producer warp
-                                    of the CTA; 32 lanes and one walker per CTA), REWL_SWEEP_LANE (one walker
-                                    per thread, walkers_per_warp walkers in each warp; lanes_per_walker must
-                                    be 0 or 1, walkers_per_block is then the walkers of a CTA, a multiple of
-                                    walkers_per_warp, at most 8 warps) */
+                                    of the CTA; 32 lanes and one walker per CTA) */
   int32_t prefetch_draws;        /* 1 = in plain mode with variant 0 the draws of the next block (sites,
                                     ln u, conflict masks) are prepared on a second stream while the current
                                     block runs, when both buffers fit in 1 GiB; 0 = no (default: kernels
@@ -121,8 +118,9 @@ typedef struct {
                                     launch; 0 = 2^34 (about 8 s at 2 GHz, while a launch takes
                                     milliseconds).  When a wait runs out both warps stop early and
                                     rewl_step returns REWL_ETIMEOUT at its next flatness check */
-  int32_t walkers_per_warp;      /* REWL_SWEEP_LANE: walkers per warp, 1..32 (lanes past it idle); 0 = as
-                                    few as spread the walkers over every SM sub-partition */
+  int32_t server_walker_target;  /* served form: no request is admitted while at least this many walkers of
+                                    windows not yet done are running (the first always is); 0 = 24 per SM,
+                                    -1 = no such limit (slots and memory only) */
 } rewl_params;
 
 /*
@@ -140,7 +138,7 @@ typedef struct {
  * ln f < lnf_final.
  */
 enum { REWL_RULE_FLAT = 0, REWL_RULE_ONE_OVER_T = 1 };
-enum { REWL_SWEEP_AUTO = -1, REWL_SWEEP_CHAIN = 0, REWL_SWEEP_STAGED = 1, REWL_SWEEP_RING = 2, REWL_SWEEP_LANE = 3 };
+enum { REWL_SWEEP_AUTO = -1, REWL_SWEEP_CHAIN = 0, REWL_SWEEP_STAGED = 1, REWL_SWEEP_RING = 2 };
 
 /* Fills *p with the defaults above. */
 void rewl_params_default(rewl_params* p);
@@ -232,8 +230,7 @@ typedef struct {
   int64_t h2d_bytes;         /* bytes copied host -> device by this handle so far */
   int64_t d2h_bytes;         /* bytes copied device -> host by this handle so far */
   int32_t prefetch_draws;    /* 1 when the next block's draws are prepared on a second stream */
-  int32_t sweep_variant;     /* the sweep form in use (REWL_SWEEP_CHAIN, _STAGED, _RING or _LANE) */
-  int32_t walkers_per_warp;  /* REWL_SWEEP_LANE: walkers per warp (else 0) */
+  int32_t sweep_variant;     /* the sweep form in use (REWL_SWEEP_CHAIN, _STAGED or _RING) */
 } rewl_info;
 
 rewl_status rewl_get_info(rewl_handle h, rewl_info* info);
@@ -291,16 +288,14 @@ rewl_status rewl_get_state(rewl_handle h, rewl_state* st);
 /*
  * rewl_autotune -- picks the sweep kernel's launch shape for one problem by
  * timing candidates on the problem itself: the ring form (32 lanes and a
- * producer warp per walker), the chain form with 32, 16, 8, 4 and 2 lanes
- * per walker (walkers per CTA as rewl_create chooses) and the lane form with
- * the walkers spread over every SM sub-partition or 1, 2, 4, 8, 16 and 32
- * walkers per warp.  Each candidate is a
+ * producer warp per walker) and the chain form with 32, 16, 8, 4 and 2 lanes
+ * per walker (walkers per CTA as rewl_create chooses).  Each candidate is a
  * fresh rewl_create with the given arguments, one warm-up block, then `sweeps`
  * sweeps timed with CUDA events around every sweep launch.  All candidates
  * compute the same bits.  results: caller array of `capacity` entries, one per
  * candidate tried (*n_results); *best: `params` (or the defaults) with
- * sweep_variant, lanes_per_walker, walkers_per_block and walkers_per_warp of
- * the fastest, ready for rewl_create.  Errors: REWL_EINVAL (arguments, sweeps not a multiple of
+ * sweep_variant, lanes_per_walker and walkers_per_block of the fastest, ready
+ * for rewl_create.  Errors: REWL_EINVAL (arguments, sweeps not a multiple of
  * sweeps_per_exchange, no candidate ran); a candidate's own failure is in its
  * result's status.
  */
@@ -309,7 +304,6 @@ typedef struct {
   int32_t status;           /* rewl_status of the candidate's run */
   double ms_per_launch;     /* mean device time of one sweep launch (sweeps_per_exchange sweeps) */
   double attempts_per_s;    /* trials per second of sweep-kernel time */
-  int32_t walkers_per_warp; /* the lane form's walkers per warp (else 0) */
 } rewl_tune_result;
 
 rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice* lattice, const int8_t* couplings,
@@ -392,21 +386,29 @@ rewl_status rewl_thermo_jackknife(const double* lng_runs, int32_t n_runs, int32_
  * result is bit-identical to the one it gets alone.
  *
  * Requests are queued at submission (inputs are copied) and admitted first
- * come, first served while a slot (max_running) and the device-memory budget
- * allow; the memory a request may need is estimated from its sizes with the
- * widest window its energy range allows.  Running requests are grouped by
- * shape (model, L).  A group advances by rounds: for every request of the
- * group one block of sweeps_per_exchange sweeps, one exchange round and,
- * when due, the flatness check -- one fused launch for the sweeps of all the
- * group's walkers (with a producer warp per walker while the GPU holds few
- * walkers, else 4 walkers of a request per CTA), one launch each for the
- * exchanges, clocks and flatness checks of all its requests.  Each group runs on a stream of its own, so
- * groups of different sizes progress side by side at their own pace.
- * rewl_server_run issues a round for every idle group and returns once at
- * least one round has finished, per unit of max_rounds.  Finished requests
- * are retired when their group's round is read: their joined ln g is read
- * back (rewl_server_result) and their memory returns to the budget.  The
- * server is internally synchronised: any thread may call it.
+ * come, first served while a slot (max_running), the device-memory budget
+ * and the target of running walkers (rewl_params.server_walker_target: the
+ * walkers of windows not yet done) allow; the memory a request may need is
+ * estimated from its sizes with the widest window its energy range allows.
+ * As windows finish, their walkers stop and make room for new requests.
+ * Running requests are grouped by shape (model, L).  A group advances by
+ * rounds: for every request of the group one block of sweeps_per_exchange
+ * sweeps, one exchange round and, when due, the flatness check -- one fused
+ * launch for the sweeps of all the group's walkers (with a producer warp per
+ * walker while the GPU holds few walkers, else 4 walkers of a request per
+ * CTA), one launch each for the exchanges, clocks and flatness checks of all
+ * its requests.  Every phase boundary is decided on the device (clocks,
+ * flatness, merges and done flags are device state; the kernels of finished
+ * windows and requests do nothing), so a group's k rounds and the report read
+ * after them are captured once as a CUDA graph and replayed, k adapted so
+ * that a replay lasts a few milliseconds.  Each group runs on a stream of its
+ * own, so groups of different sizes progress side by side at their own pace.
+ * rewl_server_run issues a replay for every idle group and returns once at
+ * least one has finished, per unit of max_rounds; it releases the server's
+ * lock while it waits on the GPU.  Finished requests are retired when their
+ * group's replay is read: their joined ln g is read back (rewl_server_result)
+ * and their memory returns to the budget.  The server is internally
+ * synchronised: any thread may call it.
  */
 typedef struct rewl_server* rewl_server_handle;
 
@@ -442,7 +444,8 @@ typedef struct {
 
 /* device_bytes: memory budget for running requests; max_running: request slots;
  * params: sweeps_per_exchange, sweeps_per_flat_check, lnf0, entry and
- * discovery budgets and allocator of every request (NULL = defaults);
+ * discovery budgets and allocator of every request, server_walker_target
+ * (NULL = defaults);
  * params.stream: NULL = one stream per shape group (groups overlap on the
  * device), else every group and request runs on that one stream (in order);
  * params.timeout_ms > 0: rewl_server_run fails with REWL_ETIMEOUT when no
@@ -453,9 +456,10 @@ rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, in
  * REWL_ENOMEM (larger than the whole budget).  Errors found at admission
  * (e.g. REWL_EENTRY) end the request in REWL_REQ_FAILED. */
 rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* r, uint64_t* id);
-/* Admits what fits, issues a round for every idle group and waits until at
- * least one round has finished; repeated up to max_rounds times (stops early
- * when nothing runs).  stats->rounds counts the group rounds finished so far.
+/* Admits what fits, issues a replay of rounds for every idle group and waits
+ * (without holding the server's lock) until at least one has finished;
+ * repeated up to max_rounds times (stops early when nothing runs).
+ * stats->rounds counts the group rounds finished so far.
  * *stats (may be NULL) describes the server afterwards.
  * Errors: REWL_ECUDA, REWL_ETIMEOUT. */
 rewl_status rewl_server_run(rewl_server_handle s, int32_t max_rounds, rewl_server_stats* stats);

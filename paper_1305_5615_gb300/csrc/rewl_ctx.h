@@ -23,7 +23,6 @@ struct rewl_ctx {
   bool own_stream = false;
   std::vector<void*> allocations;
   int G = 32, wpb = 1;
-  int wpw = 0;                  // lane form: walkers per warp
   int n_sm = 152;               // streaming multiprocessors of the device
   int n_active = 0;
   int n_done = 0;

@@ -133,23 +133,6 @@ static bool is_pow2_double(double v) {
 // are spread over all SMs; many walkers share warps.
 static void choose_config(rewl_ctx* c, int n_sm) {
   const Problem& P = c->P;
-  if (c->params.sweep_variant == kSweepLane) {
-    // one walker per thread; few walkers per warp, so that the walkers spread over every SM
-    // sub-partition (4 per SM) before two share one; up to 4 warps per CTA while that still fills the SMs
-    int wpw = c->params.walkers_per_warp;
-    if (wpw == 0) wpw = std::max(1, std::min(32, (P.n_walkers + 4 * n_sm - 1) / (4 * n_sm)));
-    int wpb = c->params.walkers_per_block;
-    if (wpb == 0) {
-      const int warps_needed = (P.n_walkers + wpw - 1) / wpw;
-      int warps = std::max(1, std::min(4, (warps_needed + n_sm - 1) / n_sm));
-      while (warps > 1 && sweep_smem_bytes(P, warps * wpw, 1, kSweepLane) > 200 * 1024) --warps;
-      wpb = warps * wpw;
-    }
-    c->G = 1;
-    c->wpw = wpw;
-    c->wpb = wpb;
-    return;
-  }
   int G = c->params.lanes_per_walker;
   if (G == 0) {
     const int nw = P.n_walkers;
@@ -300,21 +283,11 @@ rewl_status rewl_create(rewl_handle* out, const rewl_model* model, const rewl_la
   const int G = prm.lanes_per_walker;
   if (G != 0 && G != 1 && G != 2 && G != 4 && G != 8 && G != 16 && G != 32)
     return fail(REWL_EINVAL, "lanes_per_walker %d", G);
-  if (prm.walkers_per_block < 0 || (G && prm.sweep_variant != kSweepLane && prm.walkers_per_block * G > 256))
+  if (prm.walkers_per_block < 0 || (G && prm.walkers_per_block * G > 256))
     return fail(REWL_EINVAL, "walkers_per_block %d", prm.walkers_per_block);
   if (prm.mode != REWL_MODE_PLAIN && prm.mode != REWL_MODE_GRAPH) return fail(REWL_EINVAL, "mode %d", prm.mode);
-  if (prm.sweep_variant < REWL_SWEEP_AUTO || prm.sweep_variant > kSweepLane)
+  if (prm.sweep_variant < REWL_SWEEP_AUTO || prm.sweep_variant > kSweepRing)
     return fail(REWL_EINVAL, "sweep_variant %d", prm.sweep_variant);
-  if (prm.walkers_per_warp < 0 || prm.walkers_per_warp > 32) return fail(REWL_EINVAL, "walkers_per_warp %d", prm.walkers_per_warp);
-  if (prm.sweep_variant == kSweepLane) {
-    if (prm.lanes_per_walker > 1) return fail(REWL_EINVAL, "the lane form runs one walker per thread");
-    if (prm.walkers_per_block != 0 &&
-        (prm.walkers_per_warp == 0 || prm.walkers_per_block % prm.walkers_per_warp != 0 ||
-         prm.walkers_per_block / prm.walkers_per_warp > 8))
-      return fail(REWL_EINVAL, "lane form: walkers_per_block must be 1..8 times walkers_per_warp");
-  } else if (prm.walkers_per_warp != 0) {
-    return fail(REWL_EINVAL, "walkers_per_warp is taken by the lane form only");
-  }
   if (prm.sweep_variant == kSweepRing && ((prm.lanes_per_walker != 0 && prm.lanes_per_walker != 32) ||
                                           prm.walkers_per_block > 1))
     return fail(REWL_EINVAL, "the ring variant runs 32 lanes and one walker per CTA");
@@ -561,7 +534,6 @@ static rewl_status enqueue_block(rewl_ctx* c, bool with_flat) {
   A.n_att = (uint32_t)(c->params.sweeps_per_exchange * c->P.N);
   A.n_active = c->n_active;
   A.wpb = c->wpb;
-  A.wpw = c->wpw;
   A.variant = c->params.sweep_variant;
   A.wait_cycles = c->params.wait_cycles > 0 ? c->params.wait_cycles : kDefaultWaitCycles;
   if (c->pre_on && !with_graph_capture(c)) {
@@ -716,7 +688,6 @@ rewl_status rewl_get_info(rewl_handle c, rewl_info* info) {
   info->d2h_bytes = (int64_t)c->d2h_bytes;
   info->prefetch_draws = c->pre_on ? 1 : 0;
   info->sweep_variant = c->params.sweep_variant;
-  info->walkers_per_warp = c->params.sweep_variant == kSweepLane ? c->wpw : 0;
   return REWL_OK;
 }
 

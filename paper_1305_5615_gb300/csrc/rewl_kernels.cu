@@ -948,158 +948,6 @@ __global__ void __launch_bounds__(64, 1) k_sweep_ring(Problem P, DevState S, Swe
 }
 
 // ---------------------------------------------------------------------------
-// The WL sweep kernel, lane form (variant kSweepLane): one walker per thread,
-// the trials of a walker applied one after another exactly as the plain
-// definition states them -- draw, proposal, energy change on the current
-// configuration, acceptance on the fixed-point shadow (guard band decided in
-// FP64 as in the other forms), update.  Nothing is staged and no conflict
-// masks are built: a thread always evaluates its trial on the configuration
-// its previous trial left.  The draw of the next trial does not depend on the
-// walker's state, so it is computed one trial ahead and its instructions fill
-// the gaps of the dependent chain.  A CTA holds `warps` warps with `wpw`
-// walkers each (lanes wpw..31 idle), so that few walkers per warp spread the
-// walkers over every SM sub-partition: with many walkers the rate is set by
-// the latency of one walker's chain, and a warp of k walkers advances k chains
-// with each instruction.  Same trials, same order, same results as the other
-// forms.  Shared memory: the shadow of ln g ([w + 16][wpb], 8 guard bins on
-// each side) and the configuration ([lat_words][wpb]), walker-interleaved.
-// ---------------------------------------------------------------------------
-template <int MODEL>
-__device__ __forceinline__ void sweep_lane_body(const Problem& P, const DevState& S, uint32_t n_att, int wpw,
-                                                const int32_t* wids, int nloc) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int wpad = P.w + 2 * kGuardBins;
-  const int wpb = (int)(blockDim.x >> 5) * wpw;  // walker slots of the CTA (the interleave stride)
-  int64_t* s_fx = reinterpret_cast<int64_t*>(smem);                   // [wpad][wpb]
-  uint32_t* s_lat = reinterpret_cast<uint32_t*>(s_fx + (size_t)wpad * wpb);
-  uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
-  const int nthr = blockDim.x;
-  const int tid = threadIdx.x;
-
-  for (int i = tid; i < nloc * wpad; i += nthr) {
-    const int l = i / wpad, bp = i - l * wpad, b = bp - kGuardBins;
-    int64_t v = 0;
-    if (b >= 0 && b < P.w) v = to_fx(double_to_bits(S.lng[(size_t)wids[l] * P.w + b]));
-    s_fx[bp * wpb + l] = v;
-  }
-  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
-    const int l = i / P.lat_words, j = i - l * P.lat_words;
-    s_lat[j * wpb + l] = S.lat[(size_t)wids[l] * P.lat_words + j];
-  }
-  if (MODEL == kEA || MODEL == kEA3)
-    for (int i = tid; i < P.j_words; i += nthr) s_J[i] = S.J[i];
-  __syncthreads();
-
-  const int lane = tid & 31;
-  const int lw = (tid >> 5) * wpw + lane;  // this thread's walker slot
-  bool valid = lane < wpw && lw < nloc;
-  int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
-  if (valid) {
-    W = wids[lw];
-    a = W / P.m;
-    wstart = S.win_start[a];
-    bin = (S.E[W] - P.e_min) / P.e_step - wstart;
-    kexp = lnf_exponent(S.lnf[a]);
-    if ((unsigned)bin >= (unsigned)window_width(P, S, a) || kexp == kBadLnf) {
-      S.status[W] = kWalkerBadInput;
-      valid = false;
-    }
-  }
-  if (valid) {
-    const int64_t lnf_fx = 1ll << (kFxBits - kexp);  // 2^-39 <= ln f <= 64 (lnf_exponent)
-    int64_t* fxp = s_fx + (size_t)kGuardBins * wpb + lw;  // fxp[b * wpb] = shadow of bin b, b in [-8, w+7]
-    int64_t fx_cur = fxp[bin * wpb];
-    uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
-    const int w = window_width(P, S, a);  // the window test; P.w is the layout stride
-    const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
-    U4 r = philox10((uint32_t)t0, (uint32_t)(t0 >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-    uint32_t i = 0;
-    while (i < n_att) {
-      // ---- fast loop; a trial in the guard band leaves it for the exact FP64 test
-#pragma unroll 1
-      for (; i < n_att; ++i) {
-        const uint64_t tn = t0 + i + 1;  // the next trial's draw, independent of this trial
-        const U4 rn = philox10((uint32_t)tn, (uint32_t)(tn >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-        int x, y;
-        uint32_t pv;
-        trial_site<MODEL>(P, r, x, y, pv);
-        const float uf = __ull2float_rn(2ull * u52_bits(r.z, r.w) + 1ull) * 0x1p-53f;
-        const int64_t thr = __float2ll_rn(logf(uf) * 1099511627776.0f);
-        const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
-        const int bn = bin + ev.dbin;
-        const bool inwin = (unsigned)bn < (unsigned)w;
-        const int64_t fxn = fxp[bn * wpb];  // in the guard bins when outside the window (|dbin| <= 4)
-        const int64_t dd = (fx_cur - fxn) - thr;
-        const bool band = ev.dbin != 0 && inwin && dd >= -kGuardFx && dd <= kGuardFx;
-        if (band) break;
-        const bool acc = ev.dbin == 0 || (inwin && dd > kGuardFx);
-        const bool mv = acc && ev.dbin != 0;
-        if (acc) s_lat[ev.widx] ^= ev.delta;
-        if (mv) fxp[bin * wpb] = fx_cur;
-        n_acc += acc;
-        fx_cur = (mv ? fxn : fx_cur) + lnf_fx;  // ln g(E) += ln f on the shadow
-        bin = mv ? bn : bin;
-        r = rn;
-      }
-      if (i >= n_att) break;
-      // ---- trial i is in the guard band: decided exactly in FP64
-      {
-        int x, y;
-        uint32_t pv;
-        trial_site<MODEL>(P, r, x, y, pv);
-        const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
-        const int bn = bin + ev.dbin;
-        const int64_t fxn = fxp[bn * wpb];
-        const bool acc = exact_accept_fx(S, P, W, kexp, bin, fx_cur, bn, fxn, u52_bits(r.z, r.w), n_tie);
-        ++n_exact;
-        const bool mv = acc;  // dbin != 0 here
-        if (acc) s_lat[ev.widx] ^= ev.delta;
-        if (mv) fxp[bin * wpb] = fx_cur;
-        n_acc += acc;
-        fx_cur = (mv ? fxn : fx_cur) + lnf_fx;
-        bin = mv ? bn : bin;
-        ++i;
-        const uint64_t tn = t0 + i;
-        r = philox10((uint32_t)tn, (uint32_t)(tn >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-      }
-    }
-    fxp[bin * wpb] = fx_cur;
-    S.E[W] = P.e_min + (wstart + bin) * P.e_step;
-    S.wl_accept[W] += n_acc;
-    S.near_ties[W] += n_tie;
-    S.exact_tests[W] += n_exact;
-  }
-  __syncthreads();
-
-  // write back: visits = (shadow_end - shadow_start) / ln f; H += visits and the same number of
-  // FP64 additions of ln f to ln g
-  for (int i = tid; i < nloc * P.w; i += nthr) {
-    const int l = i / P.w, b = i - l * P.w;
-    const int Wl = wids[l];
-    const size_t g = (size_t)Wl * P.w + b;
-    const uint64_t v0 = double_to_bits(S.lng[g]);
-    const int kx = lnf_exponent(S.lnf[Wl / P.m]);
-    if (kx == kBadLnf) continue;  // a skipped walker: nothing ran
-    const uint32_t c = (uint32_t)((s_fx[(b + kGuardBins) * wpb + l] - to_fx(v0)) >> (kFxBits - kx));
-    if (c) {
-      S.lng[g] = bits_to_double(add_pow2_repeated(v0, kx, c));
-      S.H[g] += c;
-    }
-  }
-  for (int i = tid; i < nloc * P.lat_words; i += nthr) {
-    const int l = i / P.lat_words, j = i - l * P.lat_words;
-    S.lat[(size_t)wids[l] * P.lat_words + j] = s_lat[j * wpb + l];
-  }
-}
-
-// CTA of A.wpb / A.wpw warps with A.wpw walkers each.
-template <int MODEL>
-__global__ void __launch_bounds__(256) k_sweep_lane(Problem P, DevState S, SweepLaunch A) {
-  const int first = blockIdx.x * A.wpb;
-  sweep_lane_body<MODEL>(P, S, A.n_att, A.wpw, S.active + first, min(A.wpb, A.n_active - first));
-}
-
-// ---------------------------------------------------------------------------
 // Draws of the next sweep launch, prepared while the current one runs (on the
 // SMs the walkers leave idle): for trial i of walker W the site, the proposed
 // Potts offset, ln u, and the conflict mask of its group of G trials -- the
@@ -1496,10 +1344,6 @@ static cudaError_t prepare_sweep_t() {
     e = cudaFuncSetAttribute(k_sweep_ring<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
   }
-  if (G == 1) {
-    e = cudaFuncSetAttribute(k_sweep_lane<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    if (e != cudaSuccess) return e;
-  }
   return cudaFuncSetAttribute(k_sweep_chain<MODEL, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
@@ -1535,11 +1379,6 @@ static cudaError_t launch_sweep_t(const Problem& P, const DevState& S, const Swe
     k_sweep_ring<MODEL><<<A.n_active, 64, smem, st>>>(P, S, A);
     return cudaGetLastError();
   }
-  if (A.variant == kSweepLane) {  // one walker per thread, A.wpw per warp
-    if (G != 1 || A.wpw < 1 || A.wpw > 32 || A.wpb % A.wpw != 0 || A.wpb / A.wpw > 8) return cudaErrorInvalidValue;
-    k_sweep_lane<MODEL><<<(A.n_active + A.wpb - 1) / A.wpb, 32 * (A.wpb / A.wpw), smem, st>>>(P, S, A);
-    return cudaGetLastError();
-  }
   const int blocks = (A.n_active + A.wpb - 1) / A.wpb;
   sweep_kernel<MODEL, G>(A.variant)<<<blocks, A.wpb * G, smem, st>>>(P, S, A);
   return cudaGetLastError();
@@ -1560,11 +1399,6 @@ static cudaError_t launch_sweep_m(int G, const Problem& P, const DevState& S, co
 }
 
 size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
-  if (variant == kSweepLane) {  // shadow with guard bins and the configuration of each walker, couplings
-    size_t b = (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
-    if (P.model == kEA || P.model == kEA3) b += (size_t)P.j_words * 4;
-    return b;
-  }
   size_t b = variant == kSweepStaged ? (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4)
                                      : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
   if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);  // the staged form's trials, or HotTrial + ColdTrial

@@ -70,9 +70,8 @@ struct DevState {
 // Sweep kernel variants (identical results): the staged form keeps H in
 // shared memory and runs a one-deep sequential chain; the chain form
 // speculates two deep and rebuilds H from the shadow; the ring form is the
-// chain form with the draws made by a second, producer warp; the lane form runs
-// one walker per thread with no staging (wpw walkers in each warp).
-enum SweepVariant : int { kSweepChain = 0, kSweepStaged = 1, kSweepRing = 2, kSweepLane = 3 };
+// chain form with the draws made by a second, producer warp.
+enum SweepVariant : int { kSweepChain = 0, kSweepStaged = 1, kSweepRing = 2 };
 
 // A trial's draw, prepared ahead of its sweep launch by k_precompute: the
 // site (x | y << 8), the proposed Potts offset (<< 16), the mask of earlier
@@ -92,7 +91,6 @@ struct SweepLaunch {
                       // trial's index is clock[0] * N, read on the device
   int n_active;       // walkers in `active`
   int wpb;            // walkers per CTA
-  int wpw;            // lane form: walkers per warp (the CTA has wpb / wpw warps)
   int variant;        // SweepVariant
   const PreTrial* pre;  // prepared draws [walker][pre_stride] or nullptr (drawn in the kernel)
   uint32_t pre_stride;

@@ -6,14 +6,23 @@
 // all take about the same time per block, so a group advances in rounds --
 // one fused sweep launch over every walker of every request of the group,
 // then one launch each for the exchanges, the clocks and the due flatness
-// checks of all its requests, and a small report read back.  Each group has
-// a CUDA stream of its own and its rounds are issued as soon as the previous
+// checks of all its requests.  The device decides every phase boundary: the
+// clocks, the flatness checks, the merges and the done flags live in device
+// memory and the kernels of a finished window or request do nothing, so
+// several rounds run back to back without the host.  A group's k rounds and
+// the small report read back after them are captured once as a CUDA graph
+// and replayed (captured again when the group's table or sweep form changes);
+// k adapts so that one replay lasts a few milliseconds.  Each group has a
+// CUDA stream of its own and its replays are issued as soon as the previous
 // one has been read, so groups of different sizes run side by side on the
 // GPU at their own pace (a 12 x 12 glass is not held back by a 32 x 32 Potts
-// lattice).  Requests that finish are retired when their group's round has
-// been read: their joined ln g is read back and their memory goes to the
-// queue.  Every request keeps its own seed, schedule and state, so its result
-// is bit-identical to the one it gets alone (rewl_create + rewl_step).
+// lattice).  Requests are admitted while request slots, the memory budget and
+// the target of active walkers (walkers of windows not done) allow, so that
+// finishing windows make room for new requests.  Requests that finish are
+// retired when their group's replay has been read: their joined ln g is read
+// back and their memory goes to the queue.  Every request keeps its own seed,
+// schedule and state, so its result is bit-identical to the one it gets alone
+// (rewl_create + rewl_step).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -72,6 +81,7 @@ struct Request {
   int group = -1, slot = -1;
   int n_done = 0;
   int64_t sweeps = 0, attempts = 0;
+  int64_t active_walkers = 0;  // walkers of windows not done (from the last report)
   std::vector<double> lng;
   int32_t n_bins = 0, e_min = 0, e_step = 0;
 };
@@ -118,9 +128,15 @@ struct Group {
   size_t smem = 0, smem_quad = 0;
   int max_pairs = 0, max_m = 1, max_h = 1;
   bool dirty = true;
+  // the captured replay: k rounds and the report, for one table and one sweep form
+  cudaGraphExec_t exec = nullptr;
+  int exec_form = -1, exec_k = 0;
+  int k = 1;                        // rounds per replay (adapted to about kReplayMs)
+  Clock::time_point t_launch;
 
   ~Group() {
     if (stream) cudaStreamSynchronize(stream);
+    if (exec) cudaGraphExecDestroy(exec);
     cudaFree(d_slots);
     cudaFree(d_rep);
     cudaFree(d_list);
@@ -144,6 +160,9 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 }  // namespace
 
+constexpr double kReplayMs = 4.0;  // target duration of one replay of a group's rounds
+constexpr int kMaxRoundsPerReplay = 16;
+
 struct rewl_server {
   std::mutex mu;
   rewl_params params{};
@@ -156,6 +175,15 @@ struct rewl_server {
   int64_t rounds = 0, attempts = 0;
   int finished = 0, failed = 0;
   int n_sm = 152;
+  int64_t walker_target = 0;  // admission stops while this many walkers are active (0 = no limit)
+
+  int64_t active_walkers() const {
+    int64_t n = 0;
+    for (const auto& gp : groups)
+      for (size_t s = 0; s < gp->slots.size(); ++s)
+        if (gp->slot_req[s]) n += reqs.at(gp->slot_req[s]).active_walkers;
+    return n;
+  }
 
   int64_t running_walkers() const {
     int64_t n = 0;
@@ -204,12 +232,15 @@ struct rewl_server {
     return (int)g.slot_req.size() - 1;
   }
 
-  // Admission: first-come first-served while a slot and the memory budget allow.
+  // Admission: first-come first-served while a slot, the memory budget and the
+  // target of active walkers allow (the first request is always admitted).
   rewl_status admit() {
+    int64_t active = active_walkers();
     while (!queue.empty()) {
       const uint64_t id = queue.front();
       Request& r = reqs[id];
       if (n_running >= max_running || in_use + r.bytes > budget) break;  // head of queue waits
+      if (walker_target > 0 && n_running > 0 && active >= walker_target) break;
       queue.pop_front();
       rewl_params p = params;
       p.stream = params.stream;  // NULL: the request gets a stream of its own for its set-up
@@ -244,6 +275,8 @@ struct rewl_server {
       r.t_admit = Clock::now();
       in_use += r.bytes;
       ++n_running;
+      r.active_walkers = h->P.n_walkers;
+      active += r.active_walkers;
       g.slot_req[s] = id;
       BatchSlot& b = g.slots[s];
       b.P = h->P;
@@ -334,6 +367,41 @@ struct rewl_server {
     if (n + nq)
       SCUDA(cudaMemcpyAsync(g.d_list, g.h_list, sizeof(BatchWalker) * (n + nq), cudaMemcpyHostToDevice, g.stream));
     g.dirty = false;
+    if (g.exec) {  // the replay read the old tables' sizes: capture again
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    return REWL_OK;
+  }
+
+  // Captures g.k rounds of the group in the given sweep form, then the slot
+  // report and its copy to the pinned host table, as one graph.
+  rewl_status capture(Group& g, int form) {
+    if (g.exec) {
+      cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+    }
+    const BatchWalker* list = form == kBatchQuad ? g.d_list + g.n_list : g.d_list;
+    const int n = form == kBatchQuad ? g.n_quad : g.n_list;
+    const size_t smem = form == kBatchQuad ? g.smem_quad : g.smem;
+    cudaGraph_t graph = nullptr;
+    SCUDA(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < g.k && e == cudaSuccess; ++r)
+      e = launch_round_batch(g.d_slots, g.hi, list, n, smem, g.max_pairs, g.max_m, g.max_h, form, g.stream);
+    if (e == cudaSuccess) e = launch_slot_report(g.d_slots, g.hi, g.d_rep, g.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g.h_rep, g.d_rep, sizeof(SlotReport) * g.hi, cudaMemcpyDeviceToHost, g.stream);
+    const cudaError_t e2 = cudaStreamEndCapture(g.stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return sfail(REWL_ECUDA, "capture of a group's rounds: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return sfail(REWL_ECUDA, "instantiate a group's rounds: %s", cudaGetErrorString(e));
+    g.exec_form = form;
+    g.exec_k = g.k;
     return REWL_OK;
   }
 
@@ -347,19 +415,16 @@ struct rewl_server {
     // few walkers on the GPU: each walker's chain has a sub-partition to itself, and a producer
     // warp per walker makes its draws (the ring form); many walkers share the SMs and their issue
     // slots, and 4 walkers per CTA with 8 lanes each share the instructions of the sequential step
-    const bool few = running_walkers() <= 8 * n_sm;
-    if (few && g.smem + ring_extra_smem() <= batch_smem_limit()) {
-      SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list, g.n_list, g.smem, g.max_pairs, g.max_m, g.max_h,
-                               kBatchRing, g.stream));
-    } else if (!few && g.smem_quad <= batch_smem_limit()) {
-      SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list + g.n_list, g.n_quad, g.smem_quad, g.max_pairs, g.max_m,
-                               g.max_h, kBatchQuad, g.stream));
-    } else {
-      SCUDA(launch_round_batch(g.d_slots, g.hi, g.d_list, g.n_list, g.smem, g.max_pairs, g.max_m, g.max_h,
-                               kBatchOne, g.stream));
+    const bool few = active_walkers() <= 8 * n_sm;
+    int form = kBatchOne;
+    if (few && g.smem + ring_extra_smem() <= batch_smem_limit()) form = kBatchRing;
+    else if (!few && g.smem_quad <= batch_smem_limit()) form = kBatchQuad;
+    if (!g.exec || g.exec_form != form || g.exec_k != g.k) {
+      rewl_status st = capture(g, form);
+      if (st != REWL_OK) return st;
     }
-    SCUDA(launch_slot_report(g.d_slots, g.hi, g.d_rep, g.stream));
-    SCUDA(cudaMemcpyAsync(g.h_rep, g.d_rep, sizeof(SlotReport) * g.hi, cudaMemcpyDeviceToHost, g.stream));
+    g.t_launch = Clock::now();
+    SCUDA(cudaGraphLaunch(g.exec, g.stream));
     SCUDA(cudaEventRecord(g.ev, g.stream));
     for (int i = 0; i < (int)g.slot_req.size(); ++i) g.launched[i] = i < g.hi ? g.slot_req[i] : 0;
     g.in_flight = true;
@@ -382,10 +447,16 @@ struct rewl_server {
     }
   }
 
-  // Reads the report of a finished round of g; retires requests whose windows are all done.
+  // Reads the report of a finished replay of g; retires requests whose windows are all done.
   void collect(Group& g) {
     g.in_flight = false;
-    ++rounds;
+    rounds += g.exec_k;
+    {  // rounds per replay: powers of two, so that one replay lasts about kReplayMs
+      const double per_round = ms_between(g.t_launch, Clock::now()) / std::max(1, g.exec_k);
+      int k = 1;
+      while (k < kMaxRoundsPerReplay && per_round * 2 * k <= kReplayMs) k *= 2;
+      g.k = k;
+    }
     for (int s = 0; s < g.hi; ++s) {
       if (!g.slot_req[s] || g.launched[s] != g.slot_req[s]) continue;  // not in that round
       Request& r = reqs[g.slot_req[s]];
@@ -398,6 +469,7 @@ struct rewl_server {
       r.ctx->xround = q.rounds;
       r.ctx->attempts = q.attempts;
       r.ctx->n_done = q.n_done;
+      r.active_walkers = (int64_t)(g.slots[s].P.h - q.n_done) * g.slots[s].P.m;
       if (q.n_done < g.slots[s].P.h) continue;
       r.lng.assign(r.ctx->P.n_bins, 0.0);
       const rewl_status st = rewl_get_lng(r.ctx, r.lng.data(), (int32_t)r.lng.size(), &r.n_bins, &r.e_min, &r.e_step);
@@ -414,37 +486,44 @@ struct rewl_server {
     }
   }
 
-  // Issues a round for every idle group with running requests, then waits until
-  // at least one round in flight has finished and collects every finished one.
-  rewl_status step() {
-    int n_flight = 0;
+  // Issues a replay for every idle group with running requests, then waits until
+  // at least one replay in flight has finished and collects every finished one.
+  // The server's lock is released while it waits on the GPU, so that other
+  // threads can submit, poll and fetch results meanwhile (groups live on the
+  // heap and stay put; a replay is collected by whichever caller finds it done).
+  rewl_status step(std::unique_lock<std::mutex>& lk) {
+    std::vector<Group*> flight;
     for (auto& gp : groups) {
       Group& g = *gp;
       if (!g.in_flight && g.running() > 0) {
         rewl_status st = launch(g);
         if (st != REWL_OK) return st;
       }
-      n_flight += g.in_flight;
+      if (g.in_flight) flight.push_back(&g);
     }
-    if (!n_flight) return REWL_OK;
+    if (flight.empty()) return REWL_OK;
     const Clock::time_point t0 = Clock::now();
+    std::vector<char> ready(flight.size());
     for (long spin = 0;; ++spin) {
+      lk.unlock();
       int got = 0;
-      for (auto& gp : groups) {
-        Group& g = *gp;
-        if (!g.in_flight) continue;
-        const cudaError_t e = cudaEventQuery(g.ev);
-        if (e == cudaErrorNotReady) continue;
-        if (e != cudaSuccess) return sfail(REWL_ECUDA, "round: %s", cudaGetErrorString(e));
-        collect(g);
-        ++got;
+      cudaError_t bad = cudaSuccess;
+      for (size_t i = 0; i < flight.size(); ++i) {
+        const cudaError_t e = cudaEventQuery(flight[i]->ev);
+        ready[i] = e == cudaSuccess;
+        got += ready[i];
+        if (e != cudaSuccess && e != cudaErrorNotReady) bad = e;
       }
-      if (got) return REWL_OK;
-      if (spin > 64) {
-        std::this_thread::sleep_for(std::chrono::microseconds(20));
-        if (params.timeout_ms > 0 && ms_between(t0, Clock::now()) > (double)params.timeout_ms)
-          return sfail(REWL_ETIMEOUT, "no round finished within %lld ms", (long long)params.timeout_ms);
+      if (!got && bad == cudaSuccess && spin > 64) std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+      if (bad != cudaSuccess) return sfail(REWL_ECUDA, "round: %s", cudaGetErrorString(bad));
+      if (got) {
+        for (size_t i = 0; i < flight.size(); ++i)
+          if (ready[i] && flight[i]->in_flight) collect(*flight[i]);
+        return REWL_OK;
       }
+      if (params.timeout_ms > 0 && ms_between(t0, Clock::now()) > (double)params.timeout_ms)
+        return sfail(REWL_ETIMEOUT, "no round finished within %lld ms", (long long)params.timeout_ms);
     }
   }
 };
@@ -467,6 +546,8 @@ rewl_status rewl_server_create(rewl_server_handle* out, int64_t device_bytes, in
   int dev = 0;
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, dev);
+  s->walker_target = s->params.server_walker_target == 0 ? 24LL * s->n_sm
+                     : s->params.server_walker_target < 0 ? 0 : s->params.server_walker_target;
   if (e != cudaSuccess) {
     delete s;
     return sfail(REWL_ECUDA, "server set-up: %s", cudaGetErrorString(e));
@@ -514,12 +595,12 @@ rewl_status rewl_server_submit(rewl_server_handle s, const rewl_request* q, uint
 
 rewl_status rewl_server_run(rewl_server_handle s, int32_t max_rounds, rewl_server_stats* stats) {
   if (!s) return sfail(REWL_EINVAL, "NULL handle");
-  std::lock_guard<std::mutex> lock(s->mu);
+  std::unique_lock<std::mutex> lock(s->mu);
   for (int32_t k = 0; k < max_rounds; ++k) {
     rewl_status st = s->admit();
     if (st != REWL_OK) return st;
     if (s->n_running == 0) break;
-    st = s->step();
+    st = s->step(lock);
     if (st != REWL_OK) return st;
   }
   rewl_status st = s->admit();  // fill slots freed by the last rounds

@@ -19,7 +19,7 @@ using namespace rewl;
 namespace {
 
 struct Candidate {
-  int32_t variant, lanes, wpb, wpw;
+  int32_t variant, lanes, wpb;
 };
 
 }  // namespace
@@ -40,15 +40,10 @@ extern "C" rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice
     rewl_set_last_error("rewl_autotune: sweeps must be a multiple of sweeps_per_exchange");
     return REWL_EINVAL;
   }
-  // candidates: the ring form (one walker per CTA with a producer warp), the chain form with 32,
-  // 16, 8, 4 and 2 lanes per walker (walkers per CTA chosen by rewl_create), and the lane form
-  // with the walkers spread over every SM sub-partition (walkers per warp chosen by rewl_create)
-  // or 1, 2, 4, 8, 16 and 32 walkers per warp
-  std::vector<Candidate> cand = {{REWL_SWEEP_RING, 32, 1, 0}, {REWL_SWEEP_CHAIN, 32, 0, 0}, {REWL_SWEEP_CHAIN, 16, 0, 0},
-                                 {REWL_SWEEP_CHAIN, 8, 0, 0},  {REWL_SWEEP_CHAIN, 4, 0, 0},  {REWL_SWEEP_CHAIN, 2, 0, 0},
-                                 {REWL_SWEEP_LANE, 1, 0, 0},   {REWL_SWEEP_LANE, 1, 0, 1},   {REWL_SWEEP_LANE, 1, 0, 2},
-                                 {REWL_SWEEP_LANE, 1, 0, 4},   {REWL_SWEEP_LANE, 1, 0, 8},   {REWL_SWEEP_LANE, 1, 0, 16},
-                                 {REWL_SWEEP_LANE, 1, 0, 32}};
+  // candidates: the ring form (one walker per CTA with a producer warp), and the chain form
+  // with 32, 16, 8, 4 and 2 lanes per walker, walkers per CTA chosen by rewl_create
+  std::vector<Candidate> cand = {{REWL_SWEEP_RING, 32, 1}, {REWL_SWEEP_CHAIN, 32, 0}, {REWL_SWEEP_CHAIN, 16, 0},
+                                 {REWL_SWEEP_CHAIN, 8, 0}, {REWL_SWEEP_CHAIN, 4, 0}, {REWL_SWEEP_CHAIN, 2, 0}};
   int n = 0, best_i = -1;
   double best_ms = 0.0;
   for (const Candidate& cd : cand) {
@@ -57,7 +52,6 @@ extern "C" rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice
     p.sweep_variant = cd.variant;
     p.lanes_per_walker = cd.lanes;
     p.walkers_per_block = cd.wpb;
-    p.walkers_per_warp = cd.wpw;
     p.mode = REWL_MODE_PLAIN;
     p.profile = 1;
     p.prefetch_draws = 0;
@@ -77,7 +71,6 @@ extern "C" rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice
     r.status = st;
     if (st == REWL_OK && i1.sweep_launches > i0.sweep_launches) {
       r.walkers_per_block = i1.walkers_per_block;
-      r.walkers_per_warp = i1.walkers_per_warp;
       r.sweep_variant = i1.sweep_variant;
       r.ms_per_launch = (i1.sweep_ms - i0.sweep_ms) / (double)(i1.sweep_launches - i0.sweep_launches);
       r.attempts_per_s = (double)(i1.attempts - i0.attempts) / ((i1.sweep_ms - i0.sweep_ms) * 1e-3);
@@ -97,6 +90,5 @@ extern "C" rewl_status rewl_autotune(const rewl_model* model, const rewl_lattice
   best->sweep_variant = results[best_i].sweep_variant;
   best->lanes_per_walker = results[best_i].lanes_per_walker;
   best->walkers_per_block = results[best_i].walkers_per_block;
-  best->walkers_per_warp = results[best_i].walkers_per_warp;
   return REWL_OK;
 }

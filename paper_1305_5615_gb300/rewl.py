@@ -57,7 +57,7 @@ class rewl_params(ctypes.Structure):
                 ("free", FREE_FN), ("alloc_user", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("sweep_variant", ctypes.c_int32), ("prefetch_draws", ctypes.c_int32), ("wl_rule", ctypes.c_int32),
                 ("window_starts", ctypes.c_void_p), ("window_widths", ctypes.c_void_p),
-                ("wait_cycles", ctypes.c_int64), ("walkers_per_warp", ctypes.c_int32)]
+                ("wait_cycles", ctypes.c_int64), ("server_walker_target", ctypes.c_int32)]
 
 
 class rewl_info(ctypes.Structure):
@@ -66,8 +66,7 @@ class rewl_info(ctypes.Structure):
                  "e_step", "lattice_words", "lanes_per_walker", "walkers_per_block", "mode", "windows_done")] + \
                [("sweep_clock", ctypes.c_int64), ("exchange_rounds", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("sweep_launches", ctypes.c_int64), ("sweep_ms", ctypes.c_double), ("h2d_bytes", ctypes.c_int64),
-                ("d2h_bytes", ctypes.c_int64), ("prefetch_draws", ctypes.c_int32), ("sweep_variant", ctypes.c_int32),
-                ("walkers_per_warp", ctypes.c_int32)]
+                ("d2h_bytes", ctypes.c_int64), ("prefetch_draws", ctypes.c_int32), ("sweep_variant", ctypes.c_int32)]
 
 
 class rewl_sweep_desc(ctypes.Structure):
@@ -98,7 +97,7 @@ class rewl_server_stats(ctypes.Structure):
 class rewl_tune_result(ctypes.Structure):
     _fields_ = [("sweep_variant", ctypes.c_int32), ("lanes_per_walker", ctypes.c_int32),
                 ("walkers_per_block", ctypes.c_int32), ("status", ctypes.c_int32), ("ms_per_launch", ctypes.c_double),
-                ("attempts_per_s", ctypes.c_double), ("walkers_per_warp", ctypes.c_int32)]
+                ("attempts_per_s", ctypes.c_double)]
 
 
 class rewl_state(ctypes.Structure):
@@ -298,16 +297,16 @@ def rewl_autotune(model, L, windows, overlap, walkers_per_window, flatness, lnf_
     p = rewl_params_default()
     p.sweeps_per_exchange, p.sweeps_per_flat_check = sweeps_per_exchange, sweeps_per_flat_check
     cpl = None if couplings is None else np.ascontiguousarray(couplings, dtype=np.int8)
-    res = (rewl_tune_result * 16)()
+    res = (rewl_tune_result * 8)()
     n = ctypes.c_int32()
     best = rewl_params()
     dim = 3 if model == EA_PM_J_3D else 2
     _check(load().rewl_autotune(ctypes.byref(rewl_model(model, q)), ctypes.byref(rewl_lattice(dim, L, L, 1)), _p(cpl),
                                 windows, overlap, walkers_per_window, flatness, lnf_final, ctypes.c_uint64(seed),
-                                ctypes.byref(p), sweeps, res, 16, ctypes.byref(n), ctypes.byref(best)), "rewl_autotune")
+                                ctypes.byref(p), sweeps, res, 8, ctypes.byref(n), ctypes.byref(best)), "rewl_autotune")
     out = [{k: getattr(res[i], k) for k, _ in rewl_tune_result._fields_} for i in range(n.value)]
     kw = {"sweep_variant": best.sweep_variant, "lanes_per_walker": best.lanes_per_walker,
-          "walkers_per_block": best.walkers_per_block, "walkers_per_warp": best.walkers_per_warp}
+          "walkers_per_block": best.walkers_per_block}
     return kw, out
 
 
@@ -367,7 +366,7 @@ class REWL:
                  entry_max_sweeps=1000, discovery_sweeps=200, timeout_ms=0, lanes_per_walker=0,
                  walkers_per_block=0, mode=MODE_PLAIN, stream=None, torch_allocator=False, profile=False,
                  sweep_variant=-1, prefetch_draws=0, wl_rule=0, window_starts=None, window_widths=None,
-                 wait_cycles=0, walkers_per_warp=0):
+                 wait_cycles=0):
         if isinstance(model, str):
             model = MODELS[model]
         p = rewl_params_default()
@@ -378,7 +377,6 @@ class REWL:
         p.sweep_variant = sweep_variant
         p.prefetch_draws = prefetch_draws
         p.wait_cycles = int(wait_cycles)
-        p.walkers_per_warp = int(walkers_per_warp)
         p.wl_rule = WL_RULES[wl_rule] if isinstance(wl_rule, str) else wl_rule
         if window_starts is not None:
             self._win = (np.ascontiguousarray(window_starts, dtype=np.int32),
@@ -432,13 +430,15 @@ class RewlServer:
     run together (rewl_server_* of include/rewl.h)."""
 
     def __init__(self, device_bytes, max_running, sweeps_per_exchange=100, sweeps_per_flat_check=1000, lnf0=1.0,
-                 entry_max_sweeps=1000, discovery_sweeps=200, stream=None, wl_rule=0, timeout_ms=0):
+                 entry_max_sweeps=1000, discovery_sweeps=200, stream=None, wl_rule=0, timeout_ms=0,
+                 walker_target=0):
         L = load()
         p = rewl_params_default()
         p.sweeps_per_exchange, p.sweeps_per_flat_check, p.lnf0 = sweeps_per_exchange, sweeps_per_flat_check, lnf0
         p.entry_max_sweeps, p.discovery_sweeps = entry_max_sweeps, discovery_sweeps
         p.wl_rule = WL_RULES[wl_rule] if isinstance(wl_rule, str) else wl_rule
         p.timeout_ms = timeout_ms
+        p.server_walker_target = int(walker_target)
         if stream is not None:
             p.stream = ctypes.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
         self._h = None

@@ -91,7 +91,8 @@ def test_binding_marshals_every_option_without_a_device():
                   sweeps_per_flat_check=1000, lnf0=1.0, entry_max_sweeps=1000, discovery_sweeps=200,
                   lanes_per_walker=32, walkers_per_block=1, mode=rewl.MODE_PLAIN, profile=True, sweep_variant=2,
                   prefetch_draws=0, wl_rule="1/t", window_starts=[0, 10, 20, 30], window_widths=[20, 20, 20, 35],
-                  wait_cycles=1 << 20, walkers_per_warp=0)
+                  wait_cycles=1 << 20)
     with pytest.raises(rewl.RewlError):
         rewl.RewlServer(device_bytes=1 << 30, max_running=4, sweeps_per_exchange=100, sweeps_per_flat_check=1000,
-                        lnf0=1.0, entry_max_sweeps=1000, discovery_sweeps=200, wl_rule="1/t", timeout_ms=1000)
+                        lnf0=1.0, entry_max_sweeps=1000, discovery_sweeps=200, wl_rule="1/t", timeout_ms=1000,
+                        walker_target=0)

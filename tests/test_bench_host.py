@@ -3,6 +3,7 @@ and the reference arm's JSON line."""
 import json
 import os
 import subprocess
+import time
 import sys
 
 import bench
@@ -105,3 +106,26 @@ def test_profile_traffic_only_for_the_profiled_source(tmp_path, monkeypatch):
     assert bench.traffic_from_profile("ising-L128-h128-m32", 2) is None
     f.write_text("kernel_source_hash = 0000000000000000\ndram_bytes_per_launch = 1234\n")
     assert bench.traffic_from_profile(bench.DEFAULT_WORKLOAD, 2) is None
+
+
+def test_plain_stream_threads_follow_arrivals_and_the_concurrency_limit(monkeypatch):
+    """The measured plain arm of the served-stream benchmark: each request
+    starts at its arrival on its own thread, at most `concurrency` at once;
+    latency = end - arrival.  With one at a time it is the FIFO queue."""
+    import bench
+
+    def fake(rewl, r):
+        time.sleep(r["dur"])
+        return (r["seed"], 10)
+
+    monkeypatch.setattr(bench, "_plain_request", fake)
+    reqs = [dict(seed=k, dur=d) for k, d in enumerate([0.30, 0.10, 0.20])]
+    arrivals = [0.0, 0.05, 0.50]
+    lat, res, wall = bench.run_plain_stream(None, reqs, arrivals, 1)
+    want = bench._fifo_latencies(arrivals, [0.30, 0.10, 0.20])
+    assert all(abs(a - b) < 0.05 for a, b in zip(lat, want)), (lat, want)
+    assert [r[0] for r in res] == [0, 1, 2]
+    lat2, _, _ = bench.run_plain_stream(None, reqs, arrivals, 3)   # no queueing: latency = own duration
+    assert all(abs(a - d) < 0.05 for a, d in zip(lat2, [0.30, 0.10, 0.20])), lat2
+    s = bench._summary(lat2 + [None], list(res) + [(None, 0)], 1.0)
+    assert s["completed"] == 3 and s["unfinished"] == 1 and s["attempts_per_s"] == 30.0

@@ -309,35 +309,3 @@ def test_ring_hand_off_wait_runs_out_and_reports_a_timeout():
     D.close()
     O, D2 = make_pair("ising", 32, 16, 0.75, 4, 0.8, 1e-8, 0)
     _parity(O, D2, [1], "after a timed-out launch")
-
-
-# ------------------------------------------------------------- the lane form
-@pytest.mark.parametrize("model,L,q,h,m,wpw", [("ising", 8, 2, 4, 2, 1), ("ising", 8, 2, 4, 2, 3),
-                                               ("ising", 33, 2, 3, 2, 32), ("ising", 40, 2, 3, 4, 0),
-                                               ("potts", 8, 10, 4, 2, 2), ("potts", 32, 10, 8, 4, 0),
-                                               ("ea", 12, 2, 4, 2, 4), ("ea3d", 4, 2, 4, 2, 1)])
-def test_lane_form(model, L, q, h, m, wpw):
-    """One walker per thread (REWL_SWEEP_LANE), with 1, 2, 3, 4 or 32
-    walkers per warp, or as many as rewl_create picks (0): the same bits as
-    the oracle."""
-    O, D = make_pair(model, L, h, 0.75, m, 0.8, 1e-6, 50 + L, q=q, sweep_variant=3, walkers_per_warp=wpw)
-    assert D.info["sweep_variant"] == 3 and D.info["lanes_per_walker"] == 1
-    _parity(O, D, [1, 9, 10], "lane %s L=%d wpw=%d" % (model, L, wpw))
-
-
-def test_lane_form_ising_L8_to_convergence():
-    O, D = make_pair("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, sweep_variant=3)
-    assert compare_states(O, D, "entry") == 0
-    for i in range(2000):
-        do, dd = run_both(O, D, 10)
-        assert do == dd
-        if i % 25 == 0 or do:
-            assert compare_states(O, D, "lane block %d" % (10 * i)) == 0
-        if do:
-            break
-    assert do and (D.state()["iteration"] == 20).all()
-
-
-def test_lane_form_ising_L128_several_walkers_per_window():
-    O, D = make_pair("ising", 128, 8, 0.75, 4, 0.8, 1e-6, 0, sweep_variant=3, walkers_per_warp=2)
-    _parity(O, D, [2, 3], "lane Ising L128 8x4")

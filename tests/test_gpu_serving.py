@@ -166,3 +166,69 @@ def test_many_walkers_take_the_plain_chain_form_and_match_alone():
             if seed in ids:
                 assert np.array_equal(S.result(ids[seed])[0].view(np.uint64), g.view(np.uint64)), seed
         S.close()
+
+
+def test_admission_by_active_walkers():
+    """With a target of 16 active walkers, a request of 8 windows x 2 walkers
+    fills it: the next request waits although a slot and memory are free, and
+    is admitted once windows of the first have finished.  Results stay
+    bit-identical to solves alone."""
+    r = dict(model="ising", L=8, windows=8, walkers_per_window=2, lnf_final=1e-3, seed=21, q=2)
+    r2 = dict(r, seed=22)
+    alone = [_alone(x) for x in (r, r2)]
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=8, walker_target=16)
+    ids = [_submit(S, r), _submit(S, r2)]
+    st = S.run(1)
+    assert st["running"] == 1 and st["queued"] == 1
+    for _ in range(100000):
+        st = S.run(20)
+        if st["finished"] == 2:
+            break
+    assert st["finished"] == 2
+    assert S.poll(ids[1])["queued_ms"] > 0
+    for rid, ((g, _, _), sweeps) in zip(ids, alone):
+        assert S.poll(rid)["sweeps"] == sweeps
+        assert np.array_equal(S.result(rid)[0].view(np.uint64), g.view(np.uint64))
+
+
+def test_submit_and_poll_do_not_wait_for_a_running_round():
+    """rewl_server_run releases the server's lock while it waits on the GPU:
+    submissions and polls from another thread return at once while a long
+    replay of rounds is in flight, and the new request is then served."""
+    import threading
+    import time
+
+    big = dict(model="ising", L=128, windows=8, walkers_per_window=4, lnf_final=1e-6, seed=5, q=2)  # ~0.1 s rounds
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=8)
+    first = _submit(S, big)
+    S.run(2)                      # the group's replay length adapts after its first replay
+    stop = threading.Event()
+
+    def drive():
+        while not stop.is_set():
+            S.run(1)
+
+    th = threading.Thread(target=drive)
+    th.start()
+    try:
+        time.sleep(0.2)
+        worst = 0.0
+        for _ in range(20):
+            t0 = time.perf_counter()
+            S.poll(first)
+            worst = max(worst, time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        rid = _submit(S, REQS[0])
+        worst = max(worst, time.perf_counter() - t0)
+        assert worst < 0.05, worst   # one round of the big request lasts about 0.1 s; the calls do not wait for it
+        for _ in range(100000):
+            if S.poll(rid)["state"] == rewl.REQ_DONE:
+                break
+            time.sleep(0.01)
+    finally:
+        stop.set()
+        th.join()
+    (g, _, _), sweeps = _alone(REQS[0])
+    assert S.poll(rid)["sweeps"] == sweeps
+    assert np.array_equal(S.result(rid)[0].view(np.uint64), g.view(np.uint64))
+    S.cancel(first)
