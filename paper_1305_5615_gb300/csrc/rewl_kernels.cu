@@ -385,17 +385,22 @@ struct StagedTrial {
 // for every trial (16 bytes, one shared-memory load) and the move itself, which
 // the sequential step does not touch: accepted moves are written to the
 // configuration by their own lanes after the group (an XOR per move), except
-// where a later trial of the group needs the configuration they leave.
+// where a later trial of the group needs the configuration they leave.  Both
+// arrays are laid out [trial of the group][walker of the CTA], so that the
+// walkers of one warp (lane 0 of each group of G lanes) read their trial j
+// from neighbouring addresses.
 struct __align__(16) HotTrial {
   int64_t thr;     // ln u in units of 2^-40
-  uint32_t pk;     // dbin + 8 | pv << 8 | x << 16 | y << 24
+  int32_t dbin;    // (E_new - E_old) / e_step on the configuration the group started from
   uint32_t mask;   // earlier trials of the group whose site lies in this trial's neighbourhood
 };
-struct __align__(8) ColdTrial {
+struct ColdTrial {
   uint32_t widx;   // lattice word the move writes
   uint32_t delta;  // the move as an XOR on that word
+  uint32_t site;   // x | y << 8 | pv << 16 (for the re-evaluation of a conflicting trial)
 };
-static_assert(sizeof(HotTrial) + sizeof(ColdTrial) == sizeof(StagedTrial), "staging size");
+static_assert(sizeof(HotTrial) == 16 && sizeof(ColdTrial) == 12, "staging size");
+constexpr size_t kChainStagingBytes = sizeof(HotTrial) + sizeof(ColdTrial);  // per walker and trial of a group
 
 template <int MODEL, int G>
 __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, SweepLaunch A) {
@@ -677,8 +682,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   PreTrial* s_ring = reinterpret_cast<PreTrial*>(smem);                                  // [kRingSlots][32]
   uint64_t* s_full = reinterpret_cast<uint64_t*>(s_ring + kRingSlots * 32);              // [kRingSlots]
   uint64_t* s_empty = s_full + kRingSlots;                                               // [kRingSlots]
-  HotTrial* s_hot = reinterpret_cast<HotTrial*>(smem + (RING ? kRingBytes : 0));         // [wpb][G]
-  ColdTrial* s_cold = reinterpret_cast<ColdTrial*>(s_hot + (G > 1 ? (size_t)wpb * G : 0));  // [wpb][G]
+  HotTrial* s_hot = reinterpret_cast<HotTrial*>(smem + (RING ? kRingBytes : 0));         // [G][wpb]
+  ColdTrial* s_cold = reinterpret_cast<ColdTrial*>(s_hot + (G > 1 ? (size_t)wpb * G : 0));  // [G][wpb]
   int64_t* s_fx = reinterpret_cast<int64_t*>(s_cold + (G > 1 ? (size_t)wpb * G : 0));      // [wpad][wpb]
   uint32_t* s_lat = reinterpret_cast<uint32_t*>(s_fx + (size_t)wpad * wpb);
   uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
@@ -745,8 +750,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     const uint32_t gm = group_mask<G>();
     const int w = window_width(P, S, a);  // the window test; P.w is the layout stride
     const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
-    HotTrial* my_hot = s_hot + (size_t)lw * G;
-    ColdTrial* my_cold = s_cold + (size_t)lw * G;
+    HotTrial* my_hot = s_hot + lw;     // trial i of this walker's group: my_hot[i * wpb]
+    ColdTrial* my_cold = s_cold + lw;
 
     const PreTrial* my_pre = pre ? pre + (size_t)W * pre_stride : nullptr;
     PreTrial nxt_pre{0u, 0u, 0};
@@ -789,14 +794,14 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           if constexpr (G > 1) M = conflict_mask<MODEL, G>(P, x, y, pv, lane, gm);
         }
         const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
-        const uint32_t pk = (uint32_t)x | ((uint32_t)y << 8);
-        tr.pk = (uint32_t)(ev.dbin + 8) | (pv << 8) | (pk << 16);
+        tr.dbin = ev.dbin;
         tr.mask = M;
         mv_own.widx = ev.widx;
         mv_own.delta = ev.delta;
+        mv_own.site = (uint32_t)x | ((uint32_t)y << 8) | (pv << 16);
         if constexpr (G > 1) {
-          my_hot[lane] = tr;
-          my_cold[lane] = mv_own;
+          my_hot[lane * wpb] = tr;
+          my_cold[lane * wpb] = mv_own;
         }
       }
       if constexpr (G > 1) __syncwarp(gm);
@@ -808,9 +813,9 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
         HotTrial cc = tr, cn = tr;  // trial j and trial j+1
         if constexpr (G > 1) {
           cc = my_hot[0];
-          cn = my_hot[n_here > 1 ? 1 : 0];
+          cn = my_hot[(n_here > 1 ? 1 : 0) * wpb];
         }
-        int dj = (int)(cc.pk & 0xffu) - 8;
+        int dj = cc.dbin;
         int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of trial 0's target bin
         int j = 0;
         while (j < n_here) {
@@ -821,8 +826,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
             // loads that do not depend on trial j's outcome first (shared-memory operations
             // issue in order and must not queue behind trial j's stores)
             HotTrial cnn = cn;
-            if constexpr (G > 1) cnn = my_hot[min(j + 2, n_here - 1)];
-            const int dn = (int)(cn.pk & 0xffu) - 8;
+            if constexpr (G > 1) cnn = my_hot[min(j + 2, n_here - 1) * wpb];
+            const int dn = cn.dbin;
             const int bn = bin + dj;
             const int64_t cand_stay = fxp[(bin + dn) * wpb];  // trial j+1's target if trial j stays
             const int64_t cand_move = fxp[(bn + dn) * wpb];   // trial j+1's target if trial j moves
@@ -854,12 +859,13 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           if (hit != 0u) {
             if constexpr (G > 1)
               for (uint32_t p = hit & ~written; p != 0u; p &= p - 1u) {
-                const ColdTrial c = my_cold[__ffs(p) - 1];
+                const ColdTrial c = my_cold[(__ffs(p) - 1) * wpb];
                 s_lat[c.widx] ^= c.delta;
               }
             written |= hit;
-            e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)((cc.pk >> 16) & 0xffu), (int)(cc.pk >> 24),
-                                   (cc.pk >> 8) & 0xffu);
+            const uint32_t site = G > 1 ? my_cold[j * wpb].site : mv_own.site;
+            e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)(site & 0xffu), (int)((site >> 8) & 0xffu),
+                                   site >> 16);
             dj = e2.dbin;
           }
           const int bn = bin + dj;
@@ -885,8 +891,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           ++j;
           if (j < n_here) {  // re-prime the fast loop: trial j+1 and j+2, and trial j's target shadow
             cc = cn;
-            if constexpr (G > 1) cn = my_hot[min(j + 1, n_here - 1)];
-            dj = (int)(cc.pk & 0xffu) - 8;
+            if constexpr (G > 1) cn = my_hot[min(j + 1, n_here - 1) * wpb];
+            dj = cc.dbin;
             fxn = fxp[(bin + dj) * wpb];
           }
         }
@@ -1401,7 +1407,7 @@ static cudaError_t launch_sweep_m(int G, const Problem& P, const DevState& S, co
 size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
   size_t b = variant == kSweepStaged ? (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4)
                                      : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
-  if (G > 1) b += (size_t)wpb * G * sizeof(StagedTrial);  // the staged form's trials, or HotTrial + ColdTrial
+  if (G > 1) b += (size_t)wpb * G * (variant == kSweepStaged ? sizeof(StagedTrial) : kChainStagingBytes);
   if (P.model == kEA || P.model == kEA3) b += (size_t)P.j_words * 4;
   if (variant == kSweepRing) b += kRingBytes;
   return b;
