@@ -1184,8 +1184,9 @@ __global__ void k_flat_merge(Problem P, DevState S) { flat_merge_body(P, S, (int
 // clock is at a multiple of their flatness period.  Every request keeps its
 // own schedule, streams and state, so its trajectory is the one it has alone.
 // ---------------------------------------------------------------------------
-// One launch for the walkers of every model: each CTA runs the body of its
-// slot's model.
+// A shape group holds one model, so each form is instantiated per model and
+// the group's launch picks the one of its model.  One walker per 32-lane CTA:
+template <int MODEL>
 __global__ void __launch_bounds__(32, 16) k_sweep_batch(const BatchSlot* __restrict__ slots,
                                                         const BatchWalker* __restrict__ list) {
   __shared__ int32_t wid;
@@ -1196,16 +1197,12 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch(const BatchSlot* __restr
   if (!slots[bw.slot].active || S.done[bw.W / P.m]) return;  // uniform over the CTA
   if (threadIdx.x == 0) wid = bw.W;
   __syncthreads();
-  switch (P.model) {
-    case kIsing: sweep_chain_body<kIsing, 32>(P, S, n_att, 1, &wid, 1); break;
-    case kPotts: sweep_chain_body<kPotts, 32>(P, S, n_att, 1, &wid, 1); break;
-    case kEA: sweep_chain_body<kEA, 32>(P, S, n_att, 1, &wid, 1); break;
-    default: sweep_chain_body<kEA3, 32>(P, S, n_att, 1, &wid, 1); break;
-  }
+  sweep_chain_body<MODEL, 32>(P, S, n_att, 1, &wid, 1);
 }
 
 // The same with a producer warp per walker (the ring form): for rounds with few
 // walkers on the GPU, where each walker's chain has an SM sub-partition of its own.
+template <int MODEL>
 __global__ void __launch_bounds__(64, 8) k_sweep_batch_ring(const BatchSlot* __restrict__ slots,
                                                             const BatchWalker* __restrict__ list) {
   __shared__ int32_t wid;
@@ -1216,12 +1213,7 @@ __global__ void __launch_bounds__(64, 8) k_sweep_batch_ring(const BatchSlot* __r
   if (!slots[bw.slot].active || S.done[bw.W / P.m]) return;  // uniform over the CTA
   if (threadIdx.x == 0) wid = bw.W;
   __syncthreads();
-  switch (P.model) {
-    case kIsing: sweep_chain_body<kIsing, 32, true>(P, S, n_att, 1, &wid, 1); break;
-    case kPotts: sweep_chain_body<kPotts, 32, true>(P, S, n_att, 1, &wid, 1); break;
-    case kEA: sweep_chain_body<kEA, 32, true>(P, S, n_att, 1, &wid, 1); break;
-    default: sweep_chain_body<kEA3, 32, true>(P, S, n_att, 1, &wid, 1); break;
-  }
+  sweep_chain_body<MODEL, 32, true>(P, S, n_att, 1, &wid, 1);
 }
 
 // For rounds with many walkers on the GPU (the chains share the SMs and the
@@ -1229,6 +1221,7 @@ __global__ void __launch_bounds__(64, 8) k_sweep_batch_ring(const BatchSlot* __r
 // lanes each, so that one instruction of the sequential step serves 4 chains.
 // Entry (slot, W0) covers walkers W0 .. W0+3 of the slot; walkers of finished
 // windows are left out.
+template <int MODEL>
 __global__ void __launch_bounds__(32, 16) k_sweep_batch_quad(const BatchSlot* __restrict__ slots,
                                                              const BatchWalker* __restrict__ list) {
   __shared__ int32_t wids[4];
@@ -1246,12 +1239,7 @@ __global__ void __launch_bounds__(32, 16) k_sweep_batch_quad(const BatchSlot* __
   }
   __syncthreads();
   if (nloc == 0) return;  // uniform over the CTA
-  switch (P.model) {
-    case kIsing: sweep_chain_body<kIsing, 8>(P, S, n_att, 4, wids, nloc); break;
-    case kPotts: sweep_chain_body<kPotts, 8>(P, S, n_att, 4, wids, nloc); break;
-    case kEA: sweep_chain_body<kEA, 8>(P, S, n_att, 4, wids, nloc); break;
-    default: sweep_chain_body<kEA3, 8>(P, S, n_att, 4, wids, nloc); break;
-  }
+  sweep_chain_body<MODEL, 8>(P, S, n_att, 4, wids, nloc);
 }
 
 __global__ void k_exchange_batch(const BatchSlot* __restrict__ slots, int max_pairs) {
@@ -1301,20 +1289,42 @@ constexpr int kBatchDynSmem = 226 * 1024;
 size_t ring_extra_smem() { return kRingBytes; }
 size_t batch_smem_limit() { return kBatchDynSmem; }
 
-cudaError_t prepare_sweep_batch() {
-  const cudaError_t e = cudaFuncSetAttribute(k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+template <int MODEL>
+static cudaError_t prepare_sweep_batch_m() {
+  cudaError_t e = cudaFuncSetAttribute(k_sweep_batch<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
   if (e != cudaSuccess) return e;
-  const cudaError_t e2 = cudaFuncSetAttribute(k_sweep_batch_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
-  if (e2 != cudaSuccess) return e2;
-  return cudaFuncSetAttribute(k_sweep_batch_ring, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  e = cudaFuncSetAttribute(k_sweep_batch_quad<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_sweep_batch_ring<MODEL>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBatchDynSmem);
+}
+
+cudaError_t prepare_sweep_batch() {
+  cudaError_t e = prepare_sweep_batch_m<kIsing>();
+  if (e == cudaSuccess) e = prepare_sweep_batch_m<kPotts>();
+  if (e == cudaSuccess) e = prepare_sweep_batch_m<kEA>();
+  if (e == cudaSuccess) e = prepare_sweep_batch_m<kEA3>();
+  return e;
+}
+
+template <int MODEL>
+static void launch_sweep_batch_m(const BatchSlot* d_slots, const BatchWalker* d_list, int n_list, size_t smem,
+                                 int form, cudaStream_t st) {
+  if (form == kBatchRing) k_sweep_batch_ring<MODEL><<<n_list, 64, smem + kRingBytes, st>>>(d_slots, d_list);
+  else if (form == kBatchQuad) k_sweep_batch_quad<MODEL><<<n_list, 32, smem, st>>>(d_slots, d_list);
+  else k_sweep_batch<MODEL><<<n_list, 32, smem, st>>>(d_slots, d_list);
 }
 
 cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, const BatchWalker* d_list, int n_list,
-                               size_t smem, int max_pairs, int max_m, int max_h, int form, cudaStream_t st) {
+                               size_t smem, int max_pairs, int max_m, int max_h, int form, int model,
+                               cudaStream_t st) {
   if (n_list > 0) {
-    if (form == kBatchRing) k_sweep_batch_ring<<<n_list, 64, smem + kRingBytes, st>>>(d_slots, d_list);
-    else if (form == kBatchQuad) k_sweep_batch_quad<<<n_list, 32, smem, st>>>(d_slots, d_list);
-    else k_sweep_batch<<<n_list, 32, smem, st>>>(d_slots, d_list);
+    switch (model) {
+      case kIsing: launch_sweep_batch_m<kIsing>(d_slots, d_list, n_list, smem, form, st); break;
+      case kPotts: launch_sweep_batch_m<kPotts>(d_slots, d_list, n_list, smem, form, st); break;
+      case kEA: launch_sweep_batch_m<kEA>(d_slots, d_list, n_list, smem, form, st); break;
+      case kEA3: launch_sweep_batch_m<kEA3>(d_slots, d_list, n_list, smem, form, st); break;
+      default: return cudaErrorInvalidValue;
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

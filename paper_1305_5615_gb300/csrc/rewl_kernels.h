@@ -25,8 +25,10 @@ cudaError_t launch_entry(const Problem& P, const DevState& S, uint64_t budget, c
 size_t ring_extra_smem();   // shared memory the ring form adds to a walker's CTA
 size_t batch_smem_limit();  // dynamic shared memory a batched sweep CTA may use
 cudaError_t prepare_sweep_batch();
+// the walkers of d_list all belong to requests of one model (a shape group)
 cudaError_t launch_round_batch(const BatchSlot* d_slots, int n_slots, const BatchWalker* d_list, int n_list,
-                               size_t smem, int max_pairs, int max_m, int max_h, int form, cudaStream_t st);
+                               size_t smem, int max_pairs, int max_m, int max_h, int form, int model,
+                               cudaStream_t st);
 // forms of the batched sweep: one walker per 32-lane CTA; the same with a producer warp
 // (list of walkers); up to 4 walkers of one request per CTA, 8 lanes each (list of quads)
 enum BatchForm : int { kBatchOne = 0, kBatchRing = 1, kBatchQuad = 2 };

@@ -388,7 +388,7 @@ struct rewl_server {
     SCUDA(cudaStreamBeginCapture(g.stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int r = 0; r < g.k && e == cudaSuccess; ++r)
-      e = launch_round_batch(g.d_slots, g.hi, list, n, smem, g.max_pairs, g.max_m, g.max_h, form, g.stream);
+      e = launch_round_batch(g.d_slots, g.hi, list, n, smem, g.max_pairs, g.max_m, g.max_h, form, g.model, g.stream);
     if (e == cudaSuccess) e = launch_slot_report(g.d_slots, g.hi, g.d_rep, g.stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(g.h_rep, g.d_rep, sizeof(SlotReport) * g.hi, cudaMemcpyDeviceToHost, g.stream);
