@@ -746,15 +746,19 @@ def run_served(args, world, rank, local):
                  "plain_capacity_requests_per_s": cap, "load_factor": -args.rate, "rate_per_s": rate}
     rng = np.random.default_rng(args.seed + 1)
     arrivals = list(np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))) if rate > 0 else [0.0] * len(reqs)
+    if calib:
+        print("calibration: %s" % json.dumps(calib), file=sys.stderr, flush=True)
     slat, sres, swall, srounds = run_served_stream(rewl, reqs, arrivals, args.slots, args.server_gb,
                                                    args.served_timeout)
     served = _summary(slat, sres, swall)
     served["rounds"] = srounds
+    print("served: %s" % json.dumps(served), file=sys.stderr, flush=True)
     plain = None
     same = None
     if not args.no_plain:
         plat, pres, pwall = run_plain_stream(rewl, reqs, arrivals, args.slots)
         plain = _summary(plat, pres, pwall)
+        print("plain: %s" % json.dumps(plain), file=sys.stderr, flush=True)
         same = all(sg is None or np.array_equal(sg.view(np.uint64), pg.view(np.uint64))
                    for (sg, _), (pg, _) in zip(sres, pres))
     if rank == 0:
@@ -1152,11 +1156,11 @@ def main():
     ap.add_argument("--tdos-oracle-limit", type=float, default=300.0,
                     help="time-to-dos: solve the seeds with the oracle in full if each takes less than this (s)")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch shapes first (rewl_autotune)")
-    ap.add_argument("--requests", type=int, default=100, help="served-stream: number of requests")
+    ap.add_argument("--requests", type=int, default=48, help="served-stream: number of requests")
     ap.add_argument("--rate", type=float, default=-0.8,
                     help="served-stream: Poisson arrivals per second; 0 = all at once; < 0: -rate x the plain "
                          "form's capacity measured in a calibration run first")
-    ap.add_argument("--calib-requests", type=int, default=64, help="served-stream: calibration backlog")
+    ap.add_argument("--calib-requests", type=int, default=32, help="served-stream: calibration backlog")
     ap.add_argument("--no-plain", action="store_true", help="served-stream: skip the plain arm")
     ap.add_argument("--slots", type=int, default=256, help="served-stream: request slots (served) and the "
                                                           "plain form's concurrent handles")

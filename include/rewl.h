@@ -391,7 +391,10 @@ rewl_status rewl_thermo_jackknife(const double* lng_runs, int32_t n_runs, int32_
  * walkers of windows not yet done) allow; the memory a request may need is
  * estimated from its sizes with the widest window its energy range allows.
  * As windows finish, their walkers stop and make room for new requests.
- * Running requests are grouped by shape (model, L).  A group advances by
+ * Running requests are grouped by shape (model, L); a shape whose round of
+ * sweeps_per_exchange sweeps lasts milliseconds gives each request a group of
+ * its own (those rounds are latency-bound per walker; fused, every request
+ * would wait for the slowest walker of all).  A group advances by
  * rounds: for every request of the group one block of sweeps_per_exchange
  * sweeps, one exchange round and, when due, the flatness check -- one fused
  * launch for the sweeps of all the group's walkers (with a producer warp per

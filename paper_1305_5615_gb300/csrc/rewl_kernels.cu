@@ -390,8 +390,9 @@ struct StagedTrial {
 // walkers of one warp (lane 0 of each group of G lanes) read their trial j
 // from neighbouring addresses.
 struct __align__(16) HotTrial {
-  int64_t thr;     // ln u in units of 2^-40
-  int32_t dbin;    // (E_new - E_old) / e_step on the configuration the group started from
+  int64_t thr;     // ln u - j ln f in units of 2^-40 (j: the trial's index in its group; see below)
+  int16_t dbin;    // (E_new - E_old) / e_step on the configuration the group started from
+  uint16_t j;      // the trial's index in its group
   uint32_t mask;   // earlier trials of the group whose site lies in this trial's neighbourhood
 };
 struct ColdTrial {
@@ -677,6 +678,10 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
                                                  long long wait_cycles = kDefaultWaitCycles) {
   static_assert(G == 1 || G == 2 || G == 4 || G == 8 || G == 16 || G == 32, "G");
   static_assert(!RING || G == 32, "the ring form runs one walker on one warp");
+  // The sequential step skips the trials it need not visit (accepted for sure, energy unchanged)
+  // when one walker owns the warp; with several walkers per warp the chains run in lockstep, the
+  // longest decides, and the skip would cost more than it saves.
+  constexpr bool kSkip = G == 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const int wpad = P.w + 2 * kGuardBins;
   PreTrial* s_ring = reinterpret_cast<PreTrial*>(smem);                                  // [kRingSlots][32]
@@ -743,7 +748,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     }
   }
   if (valid) {
-    const int64_t lnf_fx = 1ll << (kFxBits - kexp);  // 2^-39 <= ln f <= 64 (lnf_exponent)
+    // 2^-39 <= ln f <= 64 (lnf_exponent): one visit adds 2^(40 - kexp) shadow units
     int64_t* fxp = s_fx + (size_t)kGuardBins * wpb + lw;  // fxp[b * wpb] = shadow of bin b, b in [-8, w+7]
     int64_t fx_cur = fxp[bin * wpb];
     uint64_t n_acc = 0, n_tie = 0, n_exact = 0;
@@ -758,9 +763,12 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     if (my_pre && (uint32_t)lane < n_att) nxt_pre = my_pre[lane];
     long long deadline = 0;
     if constexpr (RING) deadline = __shfl_sync(0xffffffffu, clock64(), 0) + wait_cycles;
+    const int lsh = kFxBits - kexp;  // ln f = 2^-kexp is 2^lsh shadow units
+    const int64_t lnf_fx = 1ll << lsh;
     for (uint32_t base = 0; base < n_att; base += G) {
       HotTrial tr;
       ColdTrial mv_own;  // this lane's move, written after the group if accepted
+      uint32_t skipm = 0;  // trials of the group the sequential step skips (accepted, energy unchanged)
       {
         int x, y;
         uint32_t pv, M = 0;
@@ -794,12 +802,24 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           if constexpr (G > 1) M = conflict_mask<MODEL, G>(P, x, y, pv, lane, gm);
         }
         const TrialEval<MODEL> ev = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, x, y, pv);
-        tr.dbin = ev.dbin;
+        tr.dbin = (int16_t)ev.dbin;
+        tr.j = (uint16_t)lane;
         tr.mask = M;
+        if constexpr (kSkip) tr.thr -= (int64_t)lane << lsh;  // the shadow clock of the group (below)
         mv_own.widx = ev.widx;
         mv_own.delta = ev.delta;
         mv_own.site = (uint32_t)x | ((uint32_t)y << 8) | (pv << 16);
-        if constexpr (G > 1) {
+        if constexpr (kSkip) {
+          // A trial that leaves the energy unchanged is accepted (min[1, g/g] = 1) and stays in its
+          // bin; when no earlier trial of the group touches its neighbourhood, that holds on the
+          // configuration it will meet, so the sequential step need not visit it: it is skipped
+          // (accepted, its ln f increment counted by the shadow clock), and the trials the step
+          // does visit are staged in order, packed.
+          const bool skip = ev.dbin == 0 && M == 0u;
+          skipm = __ballot_sync(0xffffffffu, skip);
+          if (!skip) my_hot[__popc(~skipm & ((1u << lane) - 1u)) * wpb] = tr;
+          my_cold[lane * wpb] = mv_own;
+        } else if constexpr (G > 1) {
           my_hot[lane * wpb] = tr;
           my_cold[lane * wpb] = mv_own;
         }
@@ -808,94 +828,113 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
 
       uint32_t pending = 0;  // accepted trials of the group whose move is not written yet
       if (lane == 0) {
+        // With the skip, the shadow clock: while the walker stays in one bin, its shadow grows by
+        // ln f per trial, skipped or not.  fxa is the current bin's shadow minus (index in the
+        // group) x ln f, so the shadow before trial j is fxa + j ln f; the staged threshold already
+        // holds -j ln f, so the fast test reads fxa directly, and only a move needs j ln f.
+        // Without it (several walkers per warp), fxa is the current bin's shadow itself.
         const int n_here = (int)min((uint32_t)G, n_att - base);
-        uint32_t accm = 0, written = 0;
-        HotTrial cc = tr, cn = tr;  // trial j and trial j+1
-        if constexpr (G > 1) {
-          cc = my_hot[0];
-          cn = my_hot[(n_here > 1 ? 1 : 0) * wpb];
-        }
-        int dj = cc.dbin;
-        int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of trial 0's target bin
-        int j = 0;
-        while (j < n_here) {
-          // ---- fast loop: no call and no large branch body inside; a trial that needs
-          //      re-evaluation (conflict) or the exact test (band) leaves the loop
+        const uint32_t valid = n_here >= 32 ? 0xffffffffu : ((1u << n_here) - 1u);
+        const uint32_t skipv = skipm & valid;
+        const int n_proc = __popc(valid & ~skipv);
+        uint32_t accm = skipv, written = 0;
+        int64_t fxa = fx_cur;
+        if (n_proc > 0) {
+          HotTrial cc = tr, cn = tr;  // the k-th and (k+1)-th visited trials
+          if constexpr (G > 1) {
+            cc = my_hot[0];
+            cn = my_hot[(n_proc > 1 ? 1 : 0) * wpb];
+          }
+          int dj = cc.dbin;
+          int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of the first visited trial's target bin
+          int k = 0;
+          while (k < n_proc) {
+            // ---- fast loop: no call and no large branch body inside; a trial that needs
+            //      re-evaluation (conflict) or the exact test (band) leaves the loop
 #pragma unroll 1
-          for (; j < n_here; ++j) {
-            // loads that do not depend on trial j's outcome first (shared-memory operations
-            // issue in order and must not queue behind trial j's stores)
-            HotTrial cnn = cn;
-            if constexpr (G > 1) cnn = my_hot[min(j + 2, n_here - 1) * wpb];
-            const int dn = cn.dbin;
+            for (; k < n_proc; ++k) {
+              // loads that do not depend on this trial's outcome first (shared-memory operations
+              // issue in order and must not queue behind this trial's stores)
+              HotTrial cnn = cn;
+              if constexpr (G > 1) cnn = my_hot[min(k + 2, n_proc - 1) * wpb];
+              const int dn = cn.dbin;
+              const int bn = bin + dj;
+              const int64_t cand_stay = fxp[(bin + dn) * wpb];  // next visited trial's target if this one stays
+              const int64_t cand_move = fxp[(bn + dn) * wpb];   // next visited trial's target if this one moves
+              // accept iff (shadow_old - shadow_new) - ln u > guard; reject iff < -guard
+              const bool inwin = (unsigned)bn < (unsigned)w;
+              const int64_t lim_acc = fxa - cc.thr - kGuardFx;
+              const int64_t lim_rej = fxa - cc.thr + kGuardFx;
+              const bool acc = dj == 0 || (inwin && fxn < lim_acc);
+              const bool band = dj != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
+              if (band || (accm & cc.mask) != 0u) break;
+              const bool mv = acc && dj != 0;
+              const int64_t jl = kSkip ? (int64_t)cc.j << lsh : 0;
+              const int64_t fx_here = fxa + jl;           // the current bin's shadow before this trial
+              if (mv) fxp[bin * wpb] = fx_here;           // write back the shadow of the bin left
+              accm |= (uint32_t)acc << (kSkip ? (int)cc.j : k);
+              const int64_t fwd = (dn == -dj) ? fx_here : cand_move;  // next target = the bin just left
+              if constexpr (kSkip) fxa = mv ? fxn - jl : fxa;  // ln g(E) += ln f on the shadow (the clock)
+              else fxa = (mv ? fxn : fxa) + lnf_fx;            // ln g(E) += ln f on the shadow
+              fxn = mv ? fwd : cand_stay;
+              bin = mv ? bn : bin;
+              cc = cn;
+              cn = cnn;
+              dj = dn;
+            }
+            if (k >= n_proc) break;
+            // ---- slow path for this trial: re-evaluate on the current configuration when an
+            //      accepted earlier trial of the group touched its neighbourhood (first writing
+            //      those moves), and decide exactly in FP64 when the fast test falls in the
+            //      guard band
+            const int j = kSkip ? (int)cc.j : k;
+            const int64_t jl = kSkip ? (int64_t)j << lsh : 0;
+            const int64_t fx_here = fxa + jl;
+            const uint32_t hit = accm & cc.mask;
+            TrialEval<MODEL> e2{};
+            if (hit != 0u) {
+              if constexpr (G > 1)
+                for (uint32_t p = hit & ~written; p != 0u; p &= p - 1u) {
+                  const ColdTrial c = my_cold[(__ffs(p) - 1) * wpb];
+                  s_lat[c.widx] ^= c.delta;
+                }
+              written |= hit;
+              const uint32_t site = G > 1 ? my_cold[j * wpb].site : mv_own.site;
+              e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)(site & 0xffu), (int)((site >> 8) & 0xffu),
+                                     site >> 16);
+              dj = e2.dbin;
+            }
             const int bn = bin + dj;
-            const int64_t cand_stay = fxp[(bin + dn) * wpb];  // trial j+1's target if trial j stays
-            const int64_t cand_move = fxp[(bn + dn) * wpb];   // trial j+1's target if trial j moves
-            // accept iff (shadow_old - shadow_new) - ln u > guard; reject iff < -guard
             const bool inwin = (unsigned)bn < (unsigned)w;
-            const int64_t lim_acc = fx_cur - cc.thr - kGuardFx;
-            const int64_t lim_rej = fx_cur - cc.thr + kGuardFx;
-            const bool acc = dj == 0 || (inwin && fxn < lim_acc);
-            const bool band = dj != 0 && inwin && fxn >= lim_acc && fxn <= lim_rej;
-            if (band || (accm & cc.mask) != 0u) break;
+            fxn = fxp[bn * wpb];
+            const int64_t dd = (fx_here - fxn) - (cc.thr + jl);
+            bool acc = dj == 0 || (inwin && dd > kGuardFx);
+            if (dj != 0 && inwin && dd >= -kGuardFx && dd <= kGuardFx) {
+              const uint64_t t = t0 + base + (uint32_t)j;
+              const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
+              acc = exact_accept_fx(S, P, W, kexp, bin, fx_here, bn, fxn, u52_bits(r.z, r.w), n_tie);
+              ++n_exact;
+            }
             const bool mv = acc && dj != 0;
-            if (mv) fxp[bin * wpb] = fx_cur;  // write back the shadow of the bin left
+            if (acc && hit != 0u) {  // a re-evaluated move is written at once
+              s_lat[e2.widx] ^= e2.delta;
+              written |= 1u << j;
+            }
+            if (mv) fxp[bin * wpb] = fx_here;
             accm |= (uint32_t)acc << j;
-            const int64_t fwd = (dn == -dj) ? fx_cur : cand_move;  // trial j+1 targets the bin just left
-            fx_cur = (mv ? fxn : fx_cur) + lnf_fx;                // ln g(E) += ln f on the shadow
-            fxn = mv ? fwd : cand_stay;
+            if constexpr (kSkip) fxa = mv ? fxn - jl : fxa;
+            else fxa = (mv ? fxn : fxa) + lnf_fx;
             bin = mv ? bn : bin;
-            cc = cn;
-            cn = cnn;
-            dj = dn;
-          }
-          if (j >= n_here) break;
-          // ---- slow path for trial j: re-evaluate on the current configuration when an
-          //      accepted earlier trial of the group touched its neighbourhood (first writing
-          //      those moves), and decide exactly in FP64 when the fast test falls in the
-          //      guard band
-          const uint32_t hit = accm & cc.mask;
-          TrialEval<MODEL> e2{};
-          if (hit != 0u) {
-            if constexpr (G > 1)
-              for (uint32_t p = hit & ~written; p != 0u; p &= p - 1u) {
-                const ColdTrial c = my_cold[(__ffs(p) - 1) * wpb];
-                s_lat[c.widx] ^= c.delta;
-              }
-            written |= hit;
-            const uint32_t site = G > 1 ? my_cold[j * wpb].site : mv_own.site;
-            e2 = eval_trial<MODEL>(P, s_lat, s_J, wpb, lw, (int)(site & 0xffu), (int)((site >> 8) & 0xffu),
-                                   site >> 16);
-            dj = e2.dbin;
-          }
-          const int bn = bin + dj;
-          const bool inwin = (unsigned)bn < (unsigned)w;
-          fxn = fxp[bn * wpb];
-          const int64_t dd = (fx_cur - fxn) - cc.thr;
-          bool acc = dj == 0 || (inwin && dd > kGuardFx);
-          if (dj != 0 && inwin && dd >= -kGuardFx && dd <= kGuardFx) {
-            const uint64_t t = t0 + base + (uint32_t)j;
-            const U4 r = philox10((uint32_t)t, (uint32_t)(t >> 32), (uint32_t)W, kTagFlip, P.seed_lo, P.seed_hi);
-            acc = exact_accept_fx(S, P, W, kexp, bin, fx_cur, bn, fxn, u52_bits(r.z, r.w), n_tie);
-            ++n_exact;
-          }
-          const bool mv = acc && dj != 0;
-          if (acc && hit != 0u) {  // a re-evaluated move is written at once
-            s_lat[e2.widx] ^= e2.delta;
-            written |= 1u << j;
-          }
-          if (mv) fxp[bin * wpb] = fx_cur;
-          accm |= (uint32_t)acc << j;
-          fx_cur = (mv ? fxn : fx_cur) + lnf_fx;
-          bin = mv ? bn : bin;
-          ++j;
-          if (j < n_here) {  // re-prime the fast loop: trial j+1 and j+2, and trial j's target shadow
-            cc = cn;
-            if constexpr (G > 1) cn = my_hot[min(j + 1, n_here - 1) * wpb];
-            dj = cc.dbin;
-            fxn = fxp[(bin + dj) * wpb];
+            ++k;
+            if (k < n_proc) {  // re-prime the fast loop: the next two visited trials, and the next's target
+              cc = cn;
+              if constexpr (G > 1) cn = my_hot[min(k + 1, n_proc - 1) * wpb];
+              dj = cc.dbin;
+              fxn = fxp[(bin + dj) * wpb];
+            }
           }
         }
+        fx_cur = kSkip ? fxa + ((int64_t)n_here << lsh) : fxa;  // the shadow after the group's last trial
         n_acc += (uint64_t)__popc(accm);
         pending = accm & ~written;
       }

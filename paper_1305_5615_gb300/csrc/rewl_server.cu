@@ -4,6 +4,9 @@
 //
 // Running requests are grouped by shape (model, L): the walkers of one group
 // all take about the same time per block, so a group advances in rounds --
+// (a shape whose round lasts milliseconds gives each request a group of its
+// own: there a round is latency-bound per walker, and a fused round would make
+// every request wait for the slowest walker of all of them) --
 // one fused sweep launch over every walker of every request of the group,
 // then one launch each for the exchanges, the clocks and the due flatness
 // checks of all its requests.  The device decides every phase boundary: the
@@ -110,6 +113,7 @@ int64_t request_bytes(const Request& r) {
 // in flight, so the staging buffers are never rewritten under a pending copy.
 struct Group {
   int model = 0, L = 0;
+  bool priv = false;                // serves one request at a time (a shape with long rounds)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaEvent_t ev = nullptr;
@@ -160,7 +164,9 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 
 }  // namespace
 
-constexpr double kReplayMs = 4.0;  // target duration of one replay of a group's rounds
+constexpr double kReplayMs = 4.0;  // target duration of one replay of a shared group's rounds
+constexpr double kPrivateReplayMs = 32.0;  // ... of a private group's (its request runs for seconds)
+constexpr double kPrivateRoundMs = 2.0;  // estimated round length from which requests get a group each
 constexpr int kMaxRoundsPerReplay = 16;
 
 struct rewl_server {
@@ -201,15 +207,20 @@ struct rewl_server {
     groups.clear();
   }
 
-  rewl_status group_for(int model, int L, int* out) {
-    for (size_t i = 0; i < groups.size(); ++i)
-      if (groups[i]->model == model && groups[i]->L == L) {
-        *out = (int)i;
-        return REWL_OK;
-      }
+  // The group a new request of shape (model, L) joins: the shape's shared group, or -- for
+  // shapes whose rounds are long (priv) -- an idle private group of the shape, else a new one.
+  rewl_status group_for(int model, int L, bool priv, int* out) {
+    for (size_t i = 0; i < groups.size(); ++i) {
+      const Group& g = *groups[i];
+      if (g.model != model || g.L != L || g.priv != priv) continue;
+      if (priv && (g.running() > 0 || g.in_flight)) continue;
+      *out = (int)i;
+      return REWL_OK;
+    }
     auto g = std::make_unique<Group>();
     g->model = model;
     g->L = L;
+    g->priv = priv;
     if (params.stream) {
       g->stream = (cudaStream_t)params.stream;
     } else {
@@ -260,8 +271,13 @@ struct rewl_server {
         ++failed;
         continue;
       }
+      // Requests of one shape share a group (one fused launch per phase for all of them) while a
+      // round is short, i.e. launch-bound; a shape whose round lasts milliseconds (one block of
+      // N x sweeps_per_exchange trials of a walker, about 75 ns each) is latency-bound per walker,
+      // and its requests get a group each, so that no request waits for another's slowest walker.
+      const double round_ms = 75e-6 * (double)h->P.N * (double)h->params.sweeps_per_exchange;
       int gi = -1;
-      const rewl_status gs = group_for(r.model.kind, r.lattice.Lx, &gi);
+      const rewl_status gs = group_for(r.model.kind, r.lattice.Lx, round_ms >= kPrivateRoundMs, &gi);
       if (gs != REWL_OK) {
         rewl_destroy(h);
         return gs;
@@ -451,10 +467,13 @@ struct rewl_server {
   void collect(Group& g) {
     g.in_flight = false;
     rounds += g.exec_k;
-    {  // rounds per replay: powers of two, so that one replay lasts about kReplayMs
+    {  // rounds per replay: powers of two, so that one replay lasts about kReplayMs (a shared group:
+       // its small requests should not wait long for their last round) or kPrivateReplayMs (a
+       // private group: fewer host round trips between the long rounds of its one request)
       const double per_round = ms_between(g.t_launch, Clock::now()) / std::max(1, g.exec_k);
+      const double target = g.priv ? kPrivateReplayMs : kReplayMs;
       int k = 1;
-      while (k < kMaxRoundsPerReplay && per_round * 2 * k <= kReplayMs) k *= 2;
+      while (k < kMaxRoundsPerReplay && per_round * 2 * k <= target) k *= 2;
       g.k = k;
     }
     for (int s = 0; s < g.hi; ++s) {

@@ -23,11 +23,12 @@ def test_shadow_guard_covers_two_trial_offsets():
 
 def test_bin_offset_packing_holds_every_offset():
     """The staged form packs the offset as dbin + 8 in 8 bits and decodes it as
-    (pk & 0xff) - 8; the chain forms stage it as a signed 32-bit field, and the
-    site of a trial as x | y << 8 | pv << 16 (x, y < 256; pv a Potts offset
-    < 16 or a cube layer < 64)."""
+    (pk & 0xff) - 8; the chain forms stage it as a signed 16-bit field beside the
+    trial's 16-bit index in its group (G <= 32), and the site of a trial as
+    x | y << 8 | pv << 16 (x, y < 256; pv a Potts offset < 16 or a cube layer
+    < 64)."""
     src = open(KERNELS).read()
     assert "(uint32_t)(ev.dbin + 8)" in src and "(int)(cur.pk & 0xffu) - 8" in src
     assert all(0 <= o + 8 <= 255 and 0 <= -o + 8 for o in MAX_TRIAL_OFFSET.values())
-    assert "int32_t dbin;" in src and "mv_own.site = (uint32_t)x | ((uint32_t)y << 8) | (pv << 16);" in src
+    assert "int16_t dbin;" in src and "uint16_t j;" in src and "mv_own.site = (uint32_t)x | ((uint32_t)y << 8) | (pv << 16);" in src
     assert "(int)(site & 0xffu), (int)((site >> 8) & 0xffu),\n" in src.replace("                                   ", "")
