@@ -612,58 +612,76 @@ def _fifo_latencies(arrivals, services):
     return lat
 
 
-def _plain_request(rewl, r):
+def _plain_request(rewl, r, stop=None):
     """One request solved in plain form on its own handle (and stream):
-    rewl_create + rewl_step to completion + rewl_get_lng.  Returns (ln g,
-    attempts)."""
+    rewl_create + rewl_step to completion + rewl_get_lng, in steps of one
+    flatness period, abandoned when `stop` (a threading.Event) is set.
+    Returns (ln g or None if abandoned, attempts)."""
     D = rewl.REWL(r["model"], r["L"], 8, OVERLAP, 4, FLATNESS, 1e-6, r["seed"], q=r["q"])
-    D.step(0)
-    g = D.lng()[0]
+    done = False
+    while not done and not (stop is not None and stop.is_set()):
+        done = D.step(SPF)
+    g = D.lng()[0] if done else None
     att = int(D.info["attempts"])
     D.close()
     return g, att
 
 
-def run_plain_stream(rewl, reqs, arrivals, concurrency):
+def run_plain_stream(rewl, reqs, arrivals, concurrency, stop_after=0.0):
     """The plain form over a stream: every request is solved by its own
     rewl_create/rewl_step handle on its own stream, started at its arrival by
     a host thread, at most `concurrency` at once (first come first served
-    beyond that).  Returns per-request latency (arrival -> result), ln g,
-    attempts, and the wall time."""
+    beyond that); with stop_after > 0 the requests still running after that
+    many seconds are abandoned.  Returns per-request latency (arrival ->
+    result; None if unfinished), (ln g, attempts) per request, and the wall
+    time."""
     n = len(reqs)
     sem = threading.Semaphore(concurrency)
-    lat, res = [None] * n, [None] * n
+    stop = threading.Event()
+    lat, res = [None] * n, [(None, 0)] * n
     err = []
     t0 = time.perf_counter()
 
     def run(k):
         try:
             with sem:
-                res[k] = _plain_request(rewl, reqs[k])
-            lat[k] = time.perf_counter() - t0 - arrivals[k]
+                if stop.is_set():
+                    return
+                res[k] = _plain_request(rewl, reqs[k], stop)
+            if res[k][0] is not None:
+                lat[k] = time.perf_counter() - t0 - arrivals[k]
         except BaseException as e:
             err.append(e)
 
     threads = []
     for k in range(n):
         delay = arrivals[k] - (time.perf_counter() - t0)
+        if stop_after > 0:
+            delay = min(delay, stop_after - (time.perf_counter() - t0))
         if delay > 0:
             time.sleep(delay)
+        if stop_after > 0 and time.perf_counter() - t0 >= stop_after:
+            break
         th = threading.Thread(target=run, args=(k,))
         th.start()
         threads.append(th)
+    if stop_after > 0:
+        while any(th.is_alive() for th in threads) and time.perf_counter() - t0 < stop_after:
+            time.sleep(0.05)
+        stop.set()
     for th in threads:
         th.join()
     if err:
         raise RuntimeError("plain solve failed: %r" % (err[0],))
-    return lat, res, time.perf_counter() - t0
+    return lat, res, min(time.perf_counter() - t0, stop_after) if stop_after > 0 else time.perf_counter() - t0
 
 
 def run_served_stream(rewl, reqs, arrivals, slots, server_gb, timeout_s):
     """The served form over a stream: each request submitted at its arrival
-    to one request server (continuous batching).  Returns per-request latency
-    (arrival -> result; None if unfinished), ln g, attempts, wall time and
-    the server's rounds."""
+    to one request server (continuous batching); stops after timeout_s
+    seconds (> 0).  Returns per-request latency (arrival -> result; None if
+    unfinished), (ln g, attempts) per request, wall time and the server's
+    rounds."""
     S = rewl.RewlServer(device_bytes=server_gb << 30, max_running=slots)
     ids, t_sub = [], []
     t0 = time.perf_counter()
@@ -715,13 +733,15 @@ def run_served(args, world, rank, local):
 
     Plain form: every request solved by its own handle (one launch per phase,
     its own stream), up to --slots at once.  Calibration (--rate < 0): a
-    backlog of --calib-requests requests of the mix through the plain form
-    gives its capacity C (requests completed per second); the stream then
-    arrives as a Poisson process at rate lambda = -rate x C (0.8 x C for
-    --rate -0.8).  The same arrivals go through the request server (served)
-    and through the plain form; p50/p99 latency from arrival to result,
-    aggregate attempts/s, and every request's ln g compared bit for bit
-    between the two."""
+    backlog of --calib-requests requests of the mix through the plain form for
+    --calib-seconds gives its capacity C (requests completed per second); the
+    stream then arrives as a Poisson process at rate lambda = -rate x C (0.8 x C
+    for --rate -0.8) for --arrival-window seconds.  The same arrivals go
+    through the request server (served) and through the plain form, each arm
+    stopped --drain seconds after the last arrival; p50/p99 latency from
+    arrival to result over the requests each arm finished and over those both
+    finished, aggregate attempts/s, and the ln g of every request both finished
+    compared bit for bit."""
     import numpy as np
     import torch
 
@@ -729,38 +749,47 @@ def run_served(args, world, rank, local):
     from paper_1305_5615_gb300 import rewl
 
     rewl.load()
-    reqs = served_requests(args.requests, args.seed)
-    if args.mix != "mixed":  # one shape only, e.g. "ising:32"
-        model, L = args.mix.split(":")
-        reqs = [dict(model=model, L=int(L), q=10 if model == "potts" else 2, seed=i) for i in range(len(reqs))]
     calib = None
     rate = args.rate
     if rate < 0:
         creq = served_requests(args.calib_requests, args.seed + 1000)
         for i, r in enumerate(creq):
             r["seed"] = 100000 + i
-        clat, cres, cwall = run_plain_stream(rewl, creq, [0.0] * len(creq), args.slots)
-        cap = len(creq) / cwall
+        clat, cres, cwall = run_plain_stream(rewl, creq, [0.0] * len(creq), args.slots, args.calib_seconds)
+        done = sum(1 for x in clat if x is not None)
+        cap = max(done, 1) / cwall
         rate = -args.rate * cap
-        calib = {"requests": len(creq), "concurrency": args.slots, "wall_s": cwall,
+        calib = {"requests": len(creq), "concurrency": args.slots, "seconds": cwall, "completed": done,
                  "plain_capacity_requests_per_s": cap, "load_factor": -args.rate, "rate_per_s": rate}
-    rng = np.random.default_rng(args.seed + 1)
-    arrivals = list(np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))) if rate > 0 else [0.0] * len(reqs)
-    if calib:
         print("calibration: %s" % json.dumps(calib), file=sys.stderr, flush=True)
-    slat, sres, swall, srounds = run_served_stream(rewl, reqs, arrivals, args.slots, args.server_gb,
-                                                   args.served_timeout)
+    rng = np.random.default_rng(args.seed + 1)
+    if rate > 0:
+        arrivals = list(np.cumsum(rng.exponential(1.0 / rate, size=100000)))
+        arrivals = [a for a in arrivals if a < args.arrival_window][:args.requests]
+    else:
+        arrivals = [0.0] * args.requests
+    reqs = served_requests(len(arrivals), args.seed)
+    if args.mix != "mixed":  # one shape only, e.g. "ising:32"
+        model, L = args.mix.split(":")
+        reqs = [dict(model=model, L=int(L), q=10 if model == "potts" else 2, seed=i) for i in range(len(reqs))]
+    horizon = (arrivals[-1] if arrivals else 0.0) + args.drain
+    slat, sres, swall, srounds = run_served_stream(rewl, reqs, arrivals, args.slots, args.server_gb, horizon)
     served = _summary(slat, sres, swall)
     served["rounds"] = srounds
     print("served: %s" % json.dumps(served), file=sys.stderr, flush=True)
-    plain = None
-    same = None
+    plain, same, both = None, None, None
     if not args.no_plain:
-        plat, pres, pwall = run_plain_stream(rewl, reqs, arrivals, args.slots)
+        plat, pres, pwall = run_plain_stream(rewl, reqs, arrivals, args.slots, horizon)
         plain = _summary(plat, pres, pwall)
         print("plain: %s" % json.dumps(plain), file=sys.stderr, flush=True)
-        same = all(sg is None or np.array_equal(sg.view(np.uint64), pg.view(np.uint64))
-                   for (sg, _), (pg, _) in zip(sres, pres))
+        idx = [k for k in range(len(reqs)) if slat[k] is not None and plat[k] is not None]
+        same = all(np.array_equal(sres[k][0].view(np.uint64), pres[k][0].view(np.uint64)) for k in idx)
+        if idx:
+            both = {"requests": len(idx),
+                    "served_p50_s": float(np.percentile([slat[k] for k in idx], 50)),
+                    "served_p99_s": float(np.percentile([slat[k] for k in idx], 99)),
+                    "plain_p50_s": float(np.percentile([plat[k] for k in idx], 50)),
+                    "plain_p99_s": float(np.percentile([plat[k] for k in idx], 99))}
     if rank == 0:
         print(json.dumps({"metric": "served DOS requests: p50/p99 arrival->result and aggregate spin-flip attempts/s, "
                                     "served vs plain",
@@ -769,12 +798,13 @@ def run_served(args, world, rank, local):
                           "config": {"workload": "served-stream", "requests": len(reqs),
                                      "desc": "+-J L in {12,16,20,24,32} (p=1/2 couplings from the request seed), "
                                              "Ising and Potts q=10 L in {16,24,32}, 1/3 each; 8 windows x 4 walkers; "
-                                             "ln f -> 1e-6; arrivals %s" % (
-                                                 "Poisson %.4g/s" % rate if rate > 0 else "all at t=0 (backlog)"),
+                                             "ln f -> 1e-6; arrivals %s; each arm stopped %.0f s after the last "
+                                             "arrival" % ("Poisson %.4g/s over %.0f s" % (rate, args.arrival_window)
+                                                          if rate > 0 else "all at t=0 (backlog)", args.drain),
                                      "slots": args.slots, "plain": "one handle per request on its own stream, up to "
                                                                    "%d at once" % args.slots},
                           "calibration": calib, "served": served, "plain": plain,
-                          "results_bit_identical_served_vs_plain": same}), flush=True)
+                          "finished_by_both": both, "results_bit_identical_served_vs_plain": same}), flush=True)
 
 
 def _first_iteration(rewl, wl, seed, max_sweeps, **kw):
@@ -1156,11 +1186,15 @@ def main():
     ap.add_argument("--tdos-oracle-limit", type=float, default=300.0,
                     help="time-to-dos: solve the seeds with the oracle in full if each takes less than this (s)")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch shapes first (rewl_autotune)")
-    ap.add_argument("--requests", type=int, default=48, help="served-stream: number of requests")
+    ap.add_argument("--requests", type=int, default=1000, help="served-stream: at most this many requests")
     ap.add_argument("--rate", type=float, default=-0.8,
                     help="served-stream: Poisson arrivals per second; 0 = all at once; < 0: -rate x the plain "
                          "form's capacity measured in a calibration run first")
     ap.add_argument("--calib-requests", type=int, default=32, help="served-stream: calibration backlog")
+    ap.add_argument("--calib-seconds", type=float, default=150.0, help="served-stream: calibration window")
+    ap.add_argument("--arrival-window", type=float, default=240.0, help="served-stream: seconds of arrivals")
+    ap.add_argument("--drain", type=float, default=240.0,
+                    help="served-stream: each arm stops this many seconds after the last arrival")
     ap.add_argument("--no-plain", action="store_true", help="served-stream: skip the plain arm")
     ap.add_argument("--slots", type=int, default=256, help="served-stream: request slots (served) and the "
                                                           "plain form's concurrent handles")

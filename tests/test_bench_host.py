@@ -114,8 +114,12 @@ def test_plain_stream_threads_follow_arrivals_and_the_concurrency_limit(monkeypa
     latency = end - arrival.  With one at a time it is the FIFO queue."""
     import bench
 
-    def fake(rewl, r):
-        time.sleep(r["dur"])
+    def fake(rewl, r, stop=None):
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < r["dur"]:
+            if stop is not None and stop.is_set():
+                return (None, 5)
+            time.sleep(0.005)
         return (r["seed"], 10)
 
     monkeypatch.setattr(bench, "_plain_request", fake)
@@ -129,3 +133,8 @@ def test_plain_stream_threads_follow_arrivals_and_the_concurrency_limit(monkeypa
     assert all(abs(a - d) < 0.05 for a, d in zip(lat2, [0.30, 0.10, 0.20])), lat2
     s = bench._summary(lat2 + [None], list(res) + [(None, 0)], 1.0)
     assert s["completed"] == 3 and s["unfinished"] == 1 and s["attempts_per_s"] == 30.0
+    # stopped after 0.35 s: the 0.3 s request finishes, the one queued behind it (one at a time,
+    # running from 0.3 s) is abandoned, the one arriving at 0.5 s never starts
+    lat3, res3, wall3 = bench.run_plain_stream(None, reqs, arrivals, 1, stop_after=0.35)
+    assert lat3[0] is not None and lat3[1] is None and lat3[2] is None
+    assert res3[1] == (None, 5) and res3[2] == (None, 0) and abs(wall3 - 0.35) < 0.05
