@@ -59,8 +59,8 @@ METRIC = "spin-flip attempts/s (REWL: WL sweeps + exchange + flatness/merge)"
 # convert) 10; the neighbourhood (periodic indices 8, addresses 10, five
 # loads, bit extraction 10, bond count 8) 41; energy change, bin and window
 # test 3; shadow load and the fixed-point test 7; configuration, shadow and
-# bin updates and counters 10.  About 116, in line with the 100-125 of the
-# survey's itemisation of a 2D Ising trial; 112 is used.
+# bin updates and counters 10.  About 116, within the 100-125 that an
+# independent itemisation of a 2D Ising trial gives; 112 is used.
 OPS_PER_ATTEMPT = 112
 N_SM = 152
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_ising_L32_h16_m4.txt")
