@@ -401,14 +401,7 @@ struct ColdTrial {
   uint32_t site;   // x | y << 8 | pv << 16 (for the re-evaluation of a conflicting trial)
 };
 static_assert(sizeof(HotTrial) == 16 && sizeof(ColdTrial) == 12, "staging size");
-// Per walker: G + 2 hot rows (the sequential step reads two trials ahead without clamping; rows
-// past the group's last visited trial hold a valid record of this launch or the neutral one the
-// launch starts with, so the speculative loads they address stay inside the guard bins) and G cold
-// rows.
-constexpr int kHotPad = 2;
-constexpr size_t chain_staging_bytes(int G) {
-  return (size_t)(G + kHotPad) * sizeof(HotTrial) + (size_t)G * sizeof(ColdTrial);
-}
+constexpr size_t kChainStagingBytes = sizeof(HotTrial) + sizeof(ColdTrial);  // per walker and trial of a group
 
 template <int MODEL, int G>
 __global__ void __launch_bounds__(256) k_sweep_spec(Problem P, DevState S, SweepLaunch A) {
@@ -694,8 +687,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   PreTrial* s_ring = reinterpret_cast<PreTrial*>(smem);                                  // [kRingSlots][32]
   uint64_t* s_full = reinterpret_cast<uint64_t*>(s_ring + kRingSlots * 32);              // [kRingSlots]
   uint64_t* s_empty = s_full + kRingSlots;                                               // [kRingSlots]
-  HotTrial* s_hot = reinterpret_cast<HotTrial*>(smem + (RING ? kRingBytes : 0));         // [G + 2][wpb]
-  ColdTrial* s_cold = reinterpret_cast<ColdTrial*>(s_hot + (G > 1 ? (size_t)wpb * (G + kHotPad) : 0));  // [G][wpb]
+  HotTrial* s_hot = reinterpret_cast<HotTrial*>(smem + (RING ? kRingBytes : 0));         // [G][wpb]
+  ColdTrial* s_cold = reinterpret_cast<ColdTrial*>(s_hot + (G > 1 ? (size_t)wpb * G : 0));  // [G][wpb]
   int64_t* s_fx = reinterpret_cast<int64_t*>(s_cold + (G > 1 ? (size_t)wpb * G : 0));      // [wpad][wpb]
   uint32_t* s_lat = reinterpret_cast<uint32_t*>(s_fx + (size_t)wpad * wpb);
   uint32_t* s_J = s_lat + (size_t)P.lat_words * wpb;
@@ -714,8 +707,6 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   }
   if (MODEL == kEA || MODEL == kEA3)
     for (int i = tid; i < P.j_words; i += nthr) s_J[i] = S.J[i];
-  if constexpr (G > 1)  // neutral staged trials (bin offset 0) until the first group writes its own
-    for (int i = tid; i < (G + kHotPad) * wpb; i += nthr) s_hot[i] = HotTrial{0, 0, 0, 0u};
   if (RING && tid == 0)
     for (int k = 0; k < kRingSlots; ++k) {
       mbar_init(&s_full[k], 32);
@@ -852,7 +843,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
           HotTrial cc = tr, cn = tr;  // the k-th and (k+1)-th visited trials
           if constexpr (G > 1) {
             cc = my_hot[0];
-            cn = my_hot[wpb];
+            cn = my_hot[(n_proc > 1 ? 1 : 0) * wpb];
           }
           int dj = cc.dbin;
           int64_t fxn = fxp[(bin + dj) * wpb];  // shadow of the first visited trial's target bin
@@ -865,7 +856,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
               // loads that do not depend on this trial's outcome first (shared-memory operations
               // issue in order and must not queue behind this trial's stores)
               HotTrial cnn = cn;
-              if constexpr (G > 1) cnn = my_hot[(k + 2) * wpb];  // k + 2 <= G + 1: a padded row
+              if constexpr (G > 1) cnn = my_hot[min(k + 2, n_proc - 1) * wpb];
               const int dn = cn.dbin;
               const int bn = bin + dj;
               const int64_t cand_stay = fxp[(bin + dn) * wpb];  // next visited trial's target if this one stays
@@ -937,7 +928,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
             ++k;
             if (k < n_proc) {  // re-prime the fast loop: the next two visited trials, and the next's target
               cc = cn;
-              if constexpr (G > 1) cn = my_hot[(k + 1) * wpb];
+              if constexpr (G > 1) cn = my_hot[min(k + 1, n_proc - 1) * wpb];
               dj = cc.dbin;
               fxn = fxp[(bin + dj) * wpb];
             }
@@ -1465,7 +1456,7 @@ static cudaError_t launch_sweep_m(int G, const Problem& P, const DevState& S, co
 size_t sweep_smem_bytes(const Problem& P, int wpb, int G, int variant) {
   size_t b = variant == kSweepStaged ? (size_t)wpb * ((size_t)P.w * 12 + (size_t)P.lat_words * 4)
                                      : (size_t)wpb * ((size_t)(P.w + 2 * kGuardBins) * 8 + (size_t)P.lat_words * 4);
-  if (G > 1) b += (size_t)wpb * (variant == kSweepStaged ? (size_t)G * sizeof(StagedTrial) : chain_staging_bytes(G));
+  if (G > 1) b += (size_t)wpb * G * (variant == kSweepStaged ? sizeof(StagedTrial) : kChainStagingBytes);
   if (P.model == kEA || P.model == kEA3) b += (size_t)P.j_words * 4;
   if (variant == kSweepRing) b += kRingBytes;
   return b;
