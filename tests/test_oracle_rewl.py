@@ -320,3 +320,23 @@ def test_invalid_arguments():
         OracleREWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, couplings=np.ones(128, np.int8))
     with pytest.raises(RuntimeError):
         OracleREWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 0, sweeps_per_exchange=30, sweeps_per_flat_check=100)
+
+
+def test_threaded_block_sweeps_equal_the_single_threaded_run():
+    """The oracle's threaded driver (disjoint walker ranges of each block swept
+    on several host threads, then the block's exchange and flatness check on
+    one) gives the same state, bit for bit, as orc_run_blocks."""
+    A = OracleREWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 23, sweeps_per_exchange=50, sweeps_per_flat_check=200)
+    B = OracleREWL("ising", 8, 4, 0.75, 2, 0.8, 1e-6, 23, sweeps_per_exchange=50, sweeps_per_flat_check=200)
+    for _ in range(5):
+        A.run_blocks(8)
+        B.run_blocks(8, threads=3)
+    wa, wb = A.walkers(), B.walkers()
+    for k in wa:
+        assert np.array_equal(wa[k].view(np.uint8), wb[k].view(np.uint8)), k
+    for k, v in A.windows().items():
+        assert np.array_equal(v, B.windows()[k]), k
+    for k, v in A.counters().items():
+        assert np.array_equal(v, B.counters()[k]), k
+    assert A.info() == B.info()
+    assert (A.windows()["iteration"] > 0).any()   # flatness checks and merges happened
