@@ -537,8 +537,10 @@ struct rewl_server {
       lk.lock();
       if (bad != cudaSuccess) return sfail(REWL_ECUDA, "round: %s", cudaGetErrorString(bad));
       if (got) {
+        // under the lock again: another caller may have collected a replay seen done above and
+        // issued the group's next one, so each group is collected only if its latest event is done
         for (size_t i = 0; i < flight.size(); ++i)
-          if (ready[i] && flight[i]->in_flight) collect(*flight[i]);
+          if (ready[i] && flight[i]->in_flight && cudaEventQuery(flight[i]->ev) == cudaSuccess) collect(*flight[i]);
         return REWL_OK;
       }
       if (params.timeout_ms > 0 && ms_between(t0, Clock::now()) > (double)params.timeout_ms)
