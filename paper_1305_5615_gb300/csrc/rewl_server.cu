@@ -191,14 +191,6 @@ struct rewl_server {
     return n;
   }
 
-  int64_t running_walkers() const {
-    int64_t n = 0;
-    for (const auto& gp : groups)
-      for (size_t s = 0; s < gp->slots.size(); ++s)
-        if (gp->slot_req[s]) n += gp->slots[s].P.n_walkers;
-    return n;
-  }
-
   ~rewl_server() {
     for (auto& g : groups)
       if (g->stream) cudaStreamSynchronize(g->stream);
