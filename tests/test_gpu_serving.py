@@ -232,3 +232,24 @@ def test_submit_and_poll_do_not_wait_for_a_running_round():
     assert S.poll(rid)["sweeps"] == sweeps
     assert np.array_equal(S.result(rid)[0].view(np.uint64), g.view(np.uint64))
     S.cancel(first)
+
+
+def test_private_groups_for_long_rounds_equal_results_alone():
+    """Requests whose round lasts milliseconds (Ising 24 x 24 and Potts 24 x 24: 57 600 trials per
+    walker per round) get a group of their own; beside them small requests share one.  Every
+    result stays bit-identical to the request solved alone."""
+    reqs = [dict(model="ising", L=24, windows=4, walkers_per_window=2, lnf_final=1e-3, seed=31, q=2),
+            dict(model="ising", L=24, windows=4, walkers_per_window=2, lnf_final=1e-3, seed=32, q=2),
+            dict(model="potts", L=24, windows=4, walkers_per_window=2, lnf_final=1e-2, seed=33, q=3),
+            dict(model="ising", L=8, windows=4, walkers_per_window=2, lnf_final=1e-4, seed=34, q=2)]
+    alone = [_alone(r) for r in reqs]
+    S = rewl.RewlServer(device_bytes=1 << 30, max_running=8)
+    ids = [_submit(S, r) for r in reqs]
+    for _ in range(100000):
+        st = S.run(20)
+        if st["finished"] + st["failed"] == len(reqs):
+            break
+    assert st["finished"] == len(reqs) and st["failed"] == 0
+    for rid, ((g, e0, de), sweeps) in zip(ids, alone):
+        assert S.poll(rid)["sweeps"] == sweeps
+        assert np.array_equal(S.result(rid)[0].view(np.uint64), g.view(np.uint64))
