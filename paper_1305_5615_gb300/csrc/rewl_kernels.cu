@@ -621,7 +621,8 @@ __device__ __noinline__ bool exact_accept_fx(const DevState& S, const Problem& P
 // records an error (DevState.error) and leaves its loop.
 // ---------------------------------------------------------------------------
 constexpr int kRingSlots = 4;
-constexpr size_t kRingBytes = (size_t)kRingSlots * 32 * sizeof(PreTrial) + 2 * kRingSlots * sizeof(uint64_t);
+// the ring, its full and empty barriers, and one 16-byte word that says which warp is the walker's
+constexpr size_t kRingBytes = (size_t)kRingSlots * 32 * sizeof(PreTrial) + 2 * kRingSlots * sizeof(uint64_t) + 16;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -669,8 +670,8 @@ __device__ __forceinline__ PreTrial make_pretrial(const Problem& P, uint64_t t, 
 }
 
 // Runs the sweeps of the nloc walkers wids[0..nloc) of one CTA (wpb walkers per CTA).
-// RING: warp-specialised form (G = 32, one walker, 64 threads: warp 0 the
-// walker, warp 1 the producer of its draws).
+// RING: warp-specialised form (G = 32, one walker, 64 threads: one warp the
+// walker, the other the producer of its draws).
 template <int MODEL, int G, bool RING = false>
 __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevState& S, uint32_t n_att, int wpb,
                                                  const int32_t* wids, int nloc, const PreTrial* pre = nullptr,
@@ -687,6 +688,7 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   PreTrial* s_ring = reinterpret_cast<PreTrial*>(smem);                                  // [kRingSlots][32]
   uint64_t* s_full = reinterpret_cast<uint64_t*>(s_ring + kRingSlots * 32);              // [kRingSlots]
   uint64_t* s_empty = s_full + kRingSlots;                                               // [kRingSlots]
+  int* s_swap = reinterpret_cast<int*>(s_empty + kRingSlots);                             // RING: 1 = roles swapped
   HotTrial* s_hot = reinterpret_cast<HotTrial*>(smem + (RING ? kRingBytes : 0));         // [G][wpb]
   ColdTrial* s_cold = reinterpret_cast<ColdTrial*>(s_hot + (G > 1 ? (size_t)wpb * G : 0));  // [G][wpb]
   int64_t* s_fx = reinterpret_cast<int64_t*>(s_cold + (G > 1 ? (size_t)wpb * G : 0));      // [wpad][wpb]
@@ -707,18 +709,35 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
   }
   if (MODEL == kEA || MODEL == kEA3)
     for (int i = tid; i < P.j_words; i += nthr) s_J[i] = S.J[i];
-  if (RING && tid == 0)
-    for (int k = 0; k < kRingSlots; ++k) {
-      mbar_init(&s_full[k], 32);
-      mbar_init(&s_empty[k], 32);
+  // RING: which warp of the CTA is the walker's.  An SM spreads its warps over its four
+  // sub-partitions by hardware slot (%warpid mod 4), and a CTA of two warps takes two neighbouring
+  // slots, so with several CTAs on one SM the first warps of all of them share the even
+  // sub-partitions.  A CTA whose first slot lies in an odd group of four gives the walker to its
+  // second warp, which spreads the chains over all four.  Only the placement depends on it: the
+  // two roles compute the same whichever warp takes them.  rtid is the thread's index in its
+  // role: [0, 32) the walker's warp, [32, 64) the producer.
+  int rtid = tid;
+  if constexpr (RING) {
+    if (tid == 0) {
+      uint32_t slot;
+      asm volatile("mov.u32 %0, %%warpid;" : "=r"(slot));
+      *s_swap = (int)((slot >> 2) & 1u);
+      for (int k = 0; k < kRingSlots; ++k) {
+        mbar_init(&s_full[k], 32);
+        mbar_init(&s_empty[k], 32);
+      }
     }
-  __syncthreads();
+    __syncthreads();
+    if (*s_swap) rtid = tid ^ 32;
+  } else {
+    __syncthreads();
+  }
 
-  if (RING && tid >= 32) {  // ---- producer warp
+  if (RING && rtid >= 32) {  // ---- producer warp
     if (nloc > 0) {
       const int W = wids[0];
       const uint64_t t0 = S.clock[0] * (uint64_t)P.N;
-      const int lane = tid - 32;
+      const int lane = rtid - 32;
       const uint32_t n_groups = (n_att + 31) / 32;
       const long long deadline = __shfl_sync(0xffffffffu, clock64(), 0) + wait_cycles;
       for (uint32_t g = 0; g < n_groups; ++g) {
@@ -733,8 +752,8 @@ __device__ __forceinline__ void sweep_chain_body(const Problem& P, const DevStat
     }
   }
 
-  const int lw = tid / G, lane = tid % G;
-  bool valid = lw < nloc && !(RING && tid >= 32);
+  const int lw = rtid / G, lane = rtid % G;
+  bool valid = lw < nloc && !(RING && rtid >= 32);
   int W = 0, a = 0, bin = 0, kexp = 0, wstart = 0;
   if (valid) {
     W = wids[lw];
@@ -986,7 +1005,7 @@ __global__ void __launch_bounds__(256, 1) k_sweep_chain(Problem P, DevState S, S
                              A.pre_stride);
 }
 
-// One walker per CTA of 64 threads (G = 32): warp 0 the walker, warp 1 its draws.
+// One walker per CTA of 64 threads (G = 32): one warp the walker, the other its draws.
 template <int MODEL>
 __global__ void __launch_bounds__(64, 1) k_sweep_ring(Problem P, DevState S, SweepLaunch A) {
   sweep_chain_body<MODEL, 32, true>(P, S, A.n_att, 1, S.active + blockIdx.x, 1, nullptr, 0, A.wait_cycles);
